@@ -1,0 +1,233 @@
+/*
+ * jv.h -- C ABI of libjavelin_gb, a GB300 (sm_103a) implementation of the
+ * hot path of Javelin (Booth & Bolet, arXiv 1812.06160): level-scheduled
+ * numeric ILU(0) on a CSR matrix's own pattern, the L and U sparse
+ * triangular solves ("stri"), CSR spmv, the dependency analysis that feeds
+ * them, and two extensions (transposed solves for a differentiable
+ * preconditioner apply, and single-precision factors inside double-precision
+ * Krylov iterations).
+ *
+ * General conventions
+ *   - Matrices are square CSR, 0-based, int32 indices, n >= 1, nnz < 2^31,
+ *     columns strictly ascending inside every row and the diagonal stored
+ *     (Sec. III, Fig. 1 visits the columns of a row in ascending order and
+ *     divides by a_{col,col}).
+ *   - Every array argument is a DEVICE pointer of the current CUDA device
+ *     unless its comment says "host".  Dense vectors with several right-hand
+ *     sides are row-major n x nrhs (element (i, c) at i * nrhs + c).
+ *   - The caller owns every value and vector buffer.  The handle copies the
+ *     pattern inside jv_analyze (the caller may free rowptr/colidx after it
+ *     returns) and owns all analysis arrays; pointers returned by jv_get_*
+ *     stay valid until jv_destroy.
+ *   - All work is enqueued on the handle's stream.  With options.check != 0
+ *     (the default) every compute call then synchronises that stream and
+ *     returns the device status of the work it enqueued; with check == 0 the
+ *     call returns after enqueueing and device-side errors (zero pivot, spin
+ *     timeout) accumulate in the handle until jv_status_sync.
+ *   - A handle may be used by one stream at a time: calls that overlap on the
+ *     device share the handle's scratch words and would race.
+ *   - Return value: JV_OK (0) or one of the negative JV_ERR_* codes below.
+ *     Host-side argument errors are detected before anything is enqueued.
+ */
+#ifndef JV_H
+#define JV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JV_OK 0
+#define JV_ERR_ARG (-1)           /* bad argument (null pointer, size, aliasing, dtype) */
+#define JV_ERR_PATTERN (-2)       /* column out of range, unsorted or duplicate; bad rowptr */
+#define JV_ERR_NO_DIAG (-3)       /* a row without its diagonal entry */
+#define JV_ERR_ZERO_PIVOT (-4)    /* u_ii == 0 or not finite (no pivoting, Sec. III) */
+#define JV_ERR_TIMEOUT (-5)       /* a sync-free wait exceeded spin_timeout_cycles */
+#define JV_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define JV_ERR_NOMEM (-7)         /* device allocation failed */
+#define JV_ERR_INTERNAL (-8)      /* analysis invariant violated */
+#define JV_ERR_NOT_CONVERGED (-9) /* Krylov driver hit its iteration limit */
+
+typedef struct jv_handle_s *jv_handle;
+
+typedef enum { JV_F64 = 0, JV_F32 = 1 } jv_dtype;
+
+/* Scheduling of the factor and the solves.
+ * LEVEL:    one launch per level (the barrier-per-level "CSR-LS" schedule of
+ *           Sec. VI; rows of a level run concurrently).
+ * SYNCFREE: one launch; rows are claimed in level order and each waits only
+ *           on its own dependencies (the point-to-point synchronisation of
+ *           Sec. III-A, Fig. 4, with per-row flags in global memory). */
+typedef enum { JV_MODE_LEVEL = 0, JV_MODE_SYNCFREE = 1 } jv_mode;
+
+/* The four dependency structures built by jv_analyze.
+ * LOWER:   lower(A), forward solve and factor (Sec. III: levels of lower(A)).
+ * UPPER:   upper(A), backward solve (levels counted from row n-1).
+ * UPPER_T: U^T, forward solve over the columns of U (adjoint).
+ * LOWER_T: L^T, backward solve over the columns of L (adjoint). */
+typedef enum { JV_LOWER = 0, JV_UPPER = 1, JV_UPPER_T = 2, JV_LOWER_T = 3 } jv_structure;
+
+typedef struct {
+    int mode;                       /* jv_mode; default JV_MODE_SYNCFREE */
+    int reorder;                    /* 1: work on B = P A P^T with P the level order of
+                                       lower(A) (Sec. III: nonzeros permuted into the level
+                                       ordering); every vector and value array passed to
+                                       the handle is then in B's order.  Default 0. */
+    int check;                      /* 1 (default): synchronise and return device status */
+    int vw_lower;                   /* lanes per row for LOWER/UPPER_T kernels; 0 = auto */
+    int vw_upper;                   /* lanes per row for UPPER/LOWER_T kernels; 0 = auto */
+    long long spin_timeout_cycles;  /* bound on every sync-free wait; 0 = default (2^32) */
+    int fault_row;                  /* TEST ONLY: this row never publishes its result, so
+                                       its dependants time out.  -1 (default) = off. */
+} jv_options;
+
+typedef struct {
+    int n, nnz;
+    int nnz_lower, nnz_upper;   /* strictly lower / strictly upper entries */
+    int nlev[4];                /* levels per jv_structure */
+    int vw[4];                  /* lanes per row chosen per jv_structure */
+    int mode, reorder;
+} jv_info;
+
+/* Fill *opt with the defaults above. */
+void jv_default_options(jv_options *opt);
+
+/* Dependency analysis (Sec. II level scheduling; Sec. III-A upper stage).
+ * n, nnz: matrix order and stored entries.  rowptr[n+1], colidx[nnz]: device
+ * CSR pattern (values are not needed).  opt: host pointer or NULL for the
+ * defaults.  stream: a cudaStream_t (NULL = legacy default stream) that
+ * becomes the handle's stream.  *out (host) receives the new handle.
+ * Validates the pattern (JV_ERR_PATTERN / JV_ERR_NO_DIAG with the offending
+ * row readable through jv_status_sync's bad_row), finds diag_ptr, builds the
+ * CSC of the pattern, the level of every row for all four jv_structure DAGs
+ * (longest dependency path, computed by peeling dependency-free rows on the
+ * GPU), the level sets (rows grouped by level, ascending row index inside a
+ * level, by a stable GPU radix sort), and the per-level work lists.  With
+ * opt->reorder it also builds B = P A P^T and analyses B.  Synchronous. */
+int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx,
+               const jv_options *opt, void *stream, jv_handle *out);
+
+/* Row of the last jv_analyze failure on this host thread (pattern or
+ * missing-diagonal errors), -1 if none or not row-specific. */
+int jv_last_bad_row(void);
+
+/* Release every device array the handle owns.  NULL is ignored. */
+void jv_destroy(jv_handle h);
+
+/* Change the handle's stream (cudaStream_t) / scheduling mode / check flag. */
+int jv_set_stream(jv_handle h, void *stream);
+int jv_set_mode(jv_handle h, int mode);
+int jv_set_check(jv_handle h, int check);
+
+/* Numeric ILU(0) -- Sec. III, Fig. 1 (up-looking, row by row; no pivoting).
+ * vals[nnz] (dtype vals_t) are A's values in the handle's order; lu[nnz]
+ * (dtype lu_t) receives L (strictly lower part, unit diagonal implied) and U
+ * (diagonal and strictly upper part) in the same pattern.  lu == vals is
+ * allowed when the dtypes match (in place); vals_t = F64 with lu_t = F32
+ * fuses the down-cast.  Arithmetic is done in lu_t with every product and
+ * difference rounded separately, in the order of Fig. 1.  The pivot test
+ * (u_ii == 0 or not finite -> JV_ERR_ZERO_PIVOT) is done in double.
+ * bad_row (host, may be NULL): the smallest failing row, or -1. */
+int jv_ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals,
+                   jv_dtype lu_t, void *lu, int *bad_row);
+
+/* Forward substitution with the unit lower factor (Sec. VI, stri):
+ * x = L^-1 b.  lu: factor from jv_ilu0_factor (dtype lu_t, which is also the
+ * arithmetic type).  b (dtype b_t) and x (dtype x_t) are n x nrhs row-major,
+ * nrhs >= 1; x must not overlap b. */
+int jv_lsolve(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+              const void *b, jv_dtype x_t, void *x, int nrhs);
+
+/* Backward substitution with U (Sec. VI): x = U^-1 b.  Same arguments. */
+int jv_usolve(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+              const void *b, jv_dtype x_t, void *x, int nrhs);
+
+/* Transposed solves for the adjoint of z = U^-1 L^-1 r (not in the paper):
+ * x = L^-T b (backward over the columns of L) and x = U^-T b (forward over
+ * the columns of U), through the CSC built by jv_analyze.  Same arguments. */
+int jv_lsolve_t(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+                const void *b, jv_dtype x_t, void *x, int nrhs);
+int jv_usolve_t(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+                const void *b, jv_dtype x_t, void *x, int nrhs);
+
+/* spmv (Sec. I; Sec. VI leaves it to future work): y = alpha A x + beta y.
+ * vals[nnz], x[n], y[n] all of dtype t; beta == 0 never reads y.
+ * x must not overlap y. */
+int jv_spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y,
+            double alpha, double beta);
+
+/* Pattern-restricted outer product for the factor gradient (not in the
+ * paper): for every entry p = (i, j) of the chosen part,
+ *   g[p] = alpha * sum_c a[i, c] * b[j, c]       (c < nrhs),
+ * which = 0: strictly lower part (gradient of L), which = 1: diagonal and
+ * strictly upper part (gradient of U).  Other entries of g are untouched.
+ * a, b: n x nrhs row-major; g[nnz]; all of dtype t. */
+int jv_masked_outer(jv_handle h, jv_dtype t, int which, const void *a,
+                    const void *b, int nrhs, double alpha, void *g);
+
+/* With opt.reorder: out[t] = in[vmap[t]] maps A-ordered values to B order
+ * (Sec. III: values copied into the level-ordered CSR). */
+int jv_permute_values(jv_handle h, jv_dtype t, const void *in, void *out);
+
+/* With opt.reorder: inverse == 0: out[r, :] = in[perm[r], :] (A order -> B
+ * order); inverse == 1: out[perm[r], :] = in[r, :].  in/out n x nrhs. */
+int jv_permute_vector(jv_handle h, jv_dtype t, int inverse, const void *in,
+                      void *out, int nrhs);
+
+/* Read-only views of the analysis (device pointers owned by the handle).
+ * Any output pointer may be NULL. */
+int jv_get_info(jv_handle h, jv_info *info);
+int jv_get_levels(jv_handle h, int which, int *nlev, const int **level_ptr,
+                  const int **level_rows, const int **lev);
+int jv_get_pattern(jv_handle h, const int **rowptr, const int **colidx,
+                   const int **diag_ptr);
+int jv_get_csc(jv_handle h, const int **colptr, const int **rowidx,
+               const int **csc2csr, const int **cdiag);
+int jv_get_perm(jv_handle h, const int **perm, const int **iperm,
+                const int **vmap);
+
+/* Synchronise the handle's stream, return the accumulated device status and
+ * clear it.  bad_row (host, may be NULL) receives the row of the error. */
+int jv_status_sync(jv_handle h, int *bad_row);
+
+/* Krylov drivers (Sec. I: CG / GMRES preconditioned by the ILU factors).
+ * All vectors are FP64; the preconditioner M = LU is applied with the factor
+ * lu of dtype lu_t (FP32 factors run FP32 solves, reading the FP64 residual
+ * and writing an FP64 preconditioned vector).  x holds x0 on entry. */
+typedef struct {
+    double tol;        /* stop when ||b - A x|| / ||b|| <= tol (default 1e-8) */
+    int maxit;         /* PCG iteration limit (default 10000) */
+    int restart;       /* FGMRES restart length m (default 30) */
+    int max_restarts;  /* FGMRES cycle limit (default 200) */
+} jv_krylov_opts;
+
+typedef struct {
+    int iters;           /* iterations (PCG) or inner Arnoldi steps (FGMRES) */
+    int converged;       /* 1 when the tolerance was met */
+    double relres;       /* recursive relative residual at exit */
+    double true_relres;  /* ||b - A x|| / ||b|| recomputed at exit */
+} jv_krylov_info;
+
+void jv_default_krylov_opts(jv_krylov_opts *o);
+
+/* Flexible (Polak-Ribiere) ILU(0)-preconditioned CG.  vals: A in FP64.
+ * Returns JV_OK, JV_ERR_NOT_CONVERGED, or an error.  info: host. */
+int jv_pcg(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu,
+           const double *b, double *x, const jv_krylov_opts *o,
+           jv_krylov_info *info);
+
+/* Right-preconditioned flexible GMRES(m), modified Gram-Schmidt Arnoldi. */
+int jv_fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu,
+              const double *b, double *x, const jv_krylov_opts *o,
+              jv_krylov_info *info);
+
+/* Number of kernels this library has launched in the process so far. */
+unsigned long long jv_launch_count(void);
+
+/* Static English text for a status code. */
+const char *jv_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JV_H */

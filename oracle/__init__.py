@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -24,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jv_oracle.c")
-_LIB = os.path.join(_HERE, "libjv_oracle.so")
+_LIB = os.path.join(_HERE, f"libjv_oracle_{platform.machine()}.so")
 _lock = threading.Lock()
 _lib = None
 

@@ -1,0 +1,436 @@
+// jv_analyze: dependency analysis on the GPU.
+//
+//  * validation + diag_ptr (Sec. III, Fig. 1 needs ascending columns and the
+//    diagonal a_{col,col});
+//  * CSC of the pattern (stable radix sort of the column indices), used for
+//    the dependants lists and for the adjoint's transposed solves;
+//  * levels of the four dependency DAGs by peeling (Sec. II: the vertices
+//    without incoming edges form a level, they are removed with their
+//    outgoing edges, repeat) -- one launch per level in batches, with the
+//    frontier sizes kept on the device;
+//  * level sets: rows grouped by level, ascending inside a level, by a stable
+//    radix sort keyed on the level, so the result is unique and bit-exact;
+//  * per-level work lists ("tasks") of up to 32/vw rows that never straddle a
+//    level boundary, for the factor and solve kernels;
+//  * optionally the symmetric permutation B = P A P^T into the level order
+//    (Sec. III: the nonzeros are permuted into the level ordering).
+#include <algorithm>
+
+#include "jv_internal.cuh"
+
+namespace jv {
+
+int halloc(jv_handle h, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return JV_ERR_NOMEM;
+    }
+    h->allocs.push_back(*p);
+    return JV_OK;
+}
+
+namespace {
+
+// Temporary device allocations released when the analysis returns.
+struct Temp {
+    std::vector<void *> ptrs;
+    ~Temp() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T> int get(T **p, size_t count) {
+        void *q = nullptr;
+        if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+            cudaGetLastError();
+            return JV_ERR_NOMEM;
+        }
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return JV_OK;
+    }
+};
+
+int bits_for(long long maxval) {
+    int b = 1;
+    while (b < 31 && (1ll << b) <= maxval) ++b;
+    return b;
+}
+
+#define JV_TRY(x)                 \
+    do {                          \
+        int rc_ = (x);            \
+        if (rc_ != JV_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------- validation
+__global__ void k_validate(int n, int nnz, const int *rowptr, const int *colidx, int *diag,
+                           unsigned long long *st, int *nnz_lower) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i == 0 && (rowptr[0] != 0 || rowptr[n] != nnz)) {
+        report(st, JV_ERR_PATTERN, 0);
+        return;
+    }
+    int s = rowptr[i], e = rowptr[i + 1];
+    if (s < 0 || e > nnz || s > e) {
+        report(st, JV_ERR_PATTERN, i);
+        return;
+    }
+    int d = -1;
+    for (int p = s; p < e; ++p) {
+        int c = colidx[p];
+        if (c < 0 || c >= n || (p > s && colidx[p - 1] >= c)) {
+            report(st, JV_ERR_PATTERN, i);
+            return;
+        }
+        if (c == i) d = p;
+    }
+    if (d < 0) {
+        report(st, JV_ERR_NO_DIAG, i);
+        return;
+    }
+    diag[i] = d;
+    atomicAdd(nnz_lower, d - s);
+}
+
+__global__ void k_row_of(int n, const int *rowptr, int *row_of) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) row_of[p] = i;
+}
+
+__global__ void k_copy_u32(const int *src, unsigned *dst, int m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) dst[i] = (unsigned)src[i];
+}
+
+__global__ void k_csc_finish(int nnz, const unsigned *col_sorted, const unsigned *pos_sorted,
+                             const int *row_of, int *rowidx, int *csc2csr, int *cdiag) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    int p = (int)pos_sorted[q];
+    int r = row_of[p];
+    rowidx[q] = r;
+    csc2csr[q] = p;
+    if ((unsigned)r == col_sorted[q]) cdiag[r] = q;
+}
+
+// ---------------------------------------------------------------- peeling
+struct Dag {
+    Span cnt_beg, cnt_end;   // number of dependencies of v = cnt_end(v) - cnt_beg(v)
+    Span dep_beg, dep_end;   // dependants of u: idx[dep_beg(u) .. dep_end(u))
+    const int *idx;
+};
+
+__global__ void k_peel_init(int n, Dag g, int *cnt, int *lev, int *front, int *size) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = g.cnt_end.at(i) - g.cnt_beg.at(i);
+    cnt[i] = c;
+    if (c == 0) {
+        lev[i] = 0;
+        front[atomicAdd(size, 1)] = i;
+    }
+}
+
+// One level: every dependant whose last dependency is removed joins the next
+// frontier with the next level number.
+__global__ void k_peel_round(Dag g, int *cnt, int *lev, int next_level, const int *fin,
+                             const int *size_in, int *fout, int *size_out) {
+    int size = *size_in;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < size; t += gridDim.x * blockDim.x) {
+        int u = fin[t];
+        int e1 = g.dep_end.at(u);
+        for (int e = g.dep_beg.at(u); e < e1; ++e) {
+            int v = g.idx[e];
+            if (atomicSub(&cnt[v], 1) == 1) {
+                lev[v] = next_level;
+                fout[atomicAdd(size_out, 1)] = v;
+            }
+        }
+    }
+}
+
+constexpr int kPeelBatch = 32;
+
+int peel_levels(jv_handle h, const Dag &g, int *lev, Temp &tmp, int *nlev_out,
+                std::vector<int> &widths) {
+    const int n = h->n;
+    cudaStream_t s = h->stream;
+    int *cnt, *fa, *fb, *sizes;
+    JV_TRY(tmp.get(&cnt, n));
+    JV_TRY(tmp.get(&fa, n));
+    JV_TRY(tmp.get(&fb, n));
+    JV_TRY(tmp.get(&sizes, kPeelBatch + 1));
+    JV_CUDA(cudaMemsetAsync(sizes, 0, (kPeelBatch + 1) * sizeof(int), s));
+    count_launch();
+    k_peel_init<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, g, cnt, lev, fa, sizes);
+    JV_CHECK_LAUNCH();
+    widths.clear();
+    int hs[kPeelBatch + 1];
+    long long total = 0;
+    const int grid = 152 * 8;
+    for (int level = 0;; level += kPeelBatch) {
+        JV_CUDA(cudaMemsetAsync(sizes + 1, 0, kPeelBatch * sizeof(int), s));
+        for (int b = 0; b < kPeelBatch; ++b) {
+            int r = level + b;
+            int *fin = (r % 2 == 0) ? fa : fb;
+            int *fout = (r % 2 == 0) ? fb : fa;
+            count_launch();
+            k_peel_round<<<grid, kBlock, 0, s>>>(g, cnt, lev, r + 1, fin, sizes + b, fout,
+                                                 sizes + b + 1);
+            JV_CHECK_LAUNCH();
+        }
+        JV_CUDA(cudaMemcpyAsync(hs, sizes, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        JV_CUDA(cudaStreamSynchronize(s));
+        for (int b = 0; b < kPeelBatch; ++b) {
+            if (hs[b] == 0) {
+                *nlev_out = level + b;
+                return total == n ? JV_OK : JV_ERR_INTERNAL;
+            }
+            widths.push_back(hs[b]);
+            total += hs[b];
+            if (total > n) return JV_ERR_INTERNAL;
+        }
+        JV_CUDA(cudaMemcpyAsync(sizes, sizes + kPeelBatch, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+int pow2_lanes(double mean) {
+    int v = 1;
+    while (v < 32 && v < mean) v <<= 1;
+    return v;
+}
+
+// Level sets of one DAG + the per-level task lists.
+int build_levelset(jv_handle h, int which, const Dag &g, int vw, Temp &tmp, unsigned *kbuf,
+                   unsigned *vbuf, unsigned *kalt, unsigned *valt, int *rtmp) {
+    const int n = h->n;
+    cudaStream_t s = h->stream;
+    LevelSet &L = h->ls[which];
+    JV_TRY(halloc_n(h, &L.lev, n));
+    JV_TRY(halloc_n(h, &L.rows, n));
+    std::vector<int> widths;
+    JV_TRY(peel_levels(h, g, L.lev, tmp, &L.nlev, widths));
+    JV_TRY(halloc_n(h, &L.ptr, L.nlev + 1));
+    // stable sort of (level, row): ascending rows inside every level
+    count_launch();
+    k_copy_u32<<<grid_for(n, kBlock), kBlock, 0, s>>>(L.lev, kbuf, n);
+    JV_CHECK_LAUNCH();
+    JV_TRY(iota_i32((int *)vbuf, n, s));
+    JV_TRY(radix_sort_pairs(kbuf, vbuf, kalt, valt, n, bits_for(L.nlev - 1), rtmp, s));
+    JV_CUDA(cudaMemcpyAsync(L.rows, vbuf, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    JV_TRY(keys_to_ptr(kbuf, n, L.ptr, L.nlev, s));
+    L.h_ptr.resize(L.nlev + 1);
+    JV_CUDA(cudaMemcpyAsync(L.h_ptr.data(), L.ptr, (L.nlev + 1) * sizeof(int),
+                            cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    for (int l = 0; l < L.nlev; ++l)
+        if (L.h_ptr[l + 1] - L.h_ptr[l] != widths[l]) return JV_ERR_INTERNAL;
+    // tasks: up to R rows of one level
+    L.vw = vw;
+    L.rows_per_task = kWarp / vw;
+    const int R = L.rows_per_task;
+    std::vector<int> lo, hi;
+    L.h_task_ptr.assign(L.nlev + 1, 0);
+    for (int l = 0; l < L.nlev; ++l) {
+        L.h_task_ptr[l] = (int)lo.size();
+        for (int a = L.h_ptr[l]; a < L.h_ptr[l + 1]; a += R) {
+            lo.push_back(a);
+            hi.push_back(std::min(a + R, L.h_ptr[l + 1]));
+        }
+    }
+    L.ntasks = (int)lo.size();
+    L.h_task_ptr[L.nlev] = L.ntasks;
+    JV_TRY(halloc_n(h, &L.task_lo, L.ntasks));
+    JV_TRY(halloc_n(h, &L.task_hi, L.ntasks));
+    JV_CUDA(cudaMemcpyAsync(L.task_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(L.task_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s));
+    JV_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    return JV_OK;
+}
+
+// ---------------------------------------------------------- full structure
+int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
+    const int n = h->n, nnz = h->nnz;
+    cudaStream_t s = h->stream;
+    Temp tmp;
+    JV_TRY(halloc_n(h, &h->rowptr, n + 1));
+    JV_TRY(halloc_n(h, &h->colidx, nnz));
+    JV_TRY(halloc_n(h, &h->diag, n));
+    JV_CUDA(cudaMemcpyAsync(h->rowptr, rowptr_src, (size_t)(n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(h->colidx, colidx_src, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+    int *cnt_l;
+    JV_TRY(tmp.get(&cnt_l, 1));
+    JV_CUDA(cudaMemsetAsync(cnt_l, 0, 4, s));
+    JV_CUDA(cudaMemsetAsync(h->status, 0xff, 8, s));
+    count_launch();
+    k_validate<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, nnz, h->rowptr, h->colidx, h->diag,
+                                                      h->status, cnt_l);
+    JV_CHECK_LAUNCH();
+    JV_CUDA(cudaMemcpyAsync(h->h_status, h->status, 8, cudaMemcpyDeviceToHost, s));
+    int h_nl = 0;
+    JV_CUDA(cudaMemcpyAsync(&h_nl, cnt_l, 4, cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    if (*h->h_status != ~0ull) return decode_status(*h->h_status, &h->bad_row);
+    h->nnz_lower = h_nl;
+    h->nnz_upper = nnz - n - h_nl;
+
+    // scratch for sorts
+    const int m = std::max(n, nnz);
+    unsigned *kbuf, *vbuf, *kalt, *valt;
+    int *rtmp, *row_of;
+    JV_TRY(tmp.get(&kbuf, m));
+    JV_TRY(tmp.get(&vbuf, m));
+    JV_TRY(tmp.get(&kalt, m));
+    JV_TRY(tmp.get(&valt, m));
+    JV_TRY(tmp.get(&rtmp, radix_tmp_ints(m)));
+    JV_TRY(tmp.get(&row_of, nnz));
+
+    // CSC
+    JV_TRY(halloc_n(h, &h->colptr, n + 1));
+    JV_TRY(halloc_n(h, &h->rowidx, nnz));
+    JV_TRY(halloc_n(h, &h->csc2csr, nnz));
+    JV_TRY(halloc_n(h, &h->cdiag, n));
+    count_launch();
+    k_row_of<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, row_of);
+    JV_CHECK_LAUNCH();
+    count_launch();
+    k_copy_u32<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(h->colidx, kbuf, nnz);
+    JV_CHECK_LAUNCH();
+    JV_TRY(iota_i32((int *)vbuf, nnz, s));
+    JV_TRY(radix_sort_pairs(kbuf, vbuf, kalt, valt, nnz, bits_for(n - 1), rtmp, s));
+    JV_TRY(keys_to_ptr(kbuf, nnz, h->colptr, n, s));
+    count_launch();
+    k_csc_finish<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, kbuf, vbuf, row_of, h->rowidx,
+                                                          h->csc2csr, h->cdiag);
+    JV_CHECK_LAUNCH();
+
+    // the four DAGs
+    const double mean_l = (double)h->nnz_lower / n, mean_u = (double)h->nnz_upper / n;
+    int vwl = h->opt.vw_lower > 0 ? h->opt.vw_lower : pow2_lanes(mean_l);
+    int vwu = h->opt.vw_upper > 0 ? h->opt.vw_upper : pow2_lanes(mean_u);
+    Dag gl{{h->rowptr, 0, 0}, {h->diag, 0, 0}, {h->cdiag, 0, 1}, {h->colptr, 1, 0}, h->rowidx};
+    Dag gu{{h->diag, 0, 1}, {h->rowptr, 1, 0}, {h->colptr, 0, 0}, {h->cdiag, 0, 0}, h->rowidx};
+    Dag gut{{h->colptr, 0, 0}, {h->cdiag, 0, 0}, {h->diag, 0, 1}, {h->rowptr, 1, 0}, h->colidx};
+    Dag glt{{h->cdiag, 0, 1}, {h->colptr, 1, 0}, {h->rowptr, 0, 0}, {h->diag, 0, 0}, h->colidx};
+    JV_TRY(build_levelset(h, JV_LOWER, gl, vwl, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_UPPER, gu, vwu, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_UPPER_T, gut, vwu, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_LOWER_T, glt, vwl, tmp, kbuf, vbuf, kalt, valt, rtmp));
+
+    double mean = (double)nnz / n;
+    h->spmv_vw = pow2_lanes(mean);
+    return JV_OK;
+}
+
+// ------------------------------------------------------------- reordering
+__global__ void k_inverse_perm(int n, const int *perm, int *iperm) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) iperm[perm[r]] = r;
+}
+__global__ void k_perm_lengths(int n, const int *rowptr, const int *perm, int *len) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) len[r] = rowptr[perm[r] + 1] - rowptr[perm[r]];
+}
+__global__ void k_perm_entries(int n, const int *rowptr, const int *colidx, const int *perm,
+                               const int *iperm, const int *browptr, unsigned *bcol,
+                               unsigned *brow, int *src) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int i = perm[r];
+    int d = browptr[r];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p, ++d) {
+        bcol[d] = (unsigned)iperm[colidx[p]];
+        brow[d] = (unsigned)r;
+        src[d] = p;
+    }
+}
+__global__ void k_gather_u32(int m, const unsigned *src, const unsigned *idx, unsigned *dst) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) dst[t] = src[idx[t]];
+}
+__global__ void k_perm_finish(int m, const unsigned *order, const unsigned *bcol, const int *src,
+                              int *colidx_out, int *vmap_out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    unsigned o = order[t];
+    colidx_out[t] = (int)bcol[o];
+    vmap_out[t] = src[o];
+}
+
+}  // namespace
+
+void free_all(jv_handle h) {
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    for (auto &L : h->ls) L = LevelSet();
+}
+
+int analyze(jv_handle h, const int *rowptr, const int *colidx) {
+    const int n = h->n, nnz = h->nnz;
+    cudaStream_t s = h->stream;
+    int rc = build_all(h, rowptr, colidx);
+    if (rc != JV_OK || !h->opt.reorder) return rc;
+
+    // B = P A P^T with P the level order of lower(A)
+    Temp tmp;
+    int *perm, *iperm, *browptr, *bcolidx, *vmap, *len, *src;
+    unsigned *bcol, *brow, *kbuf, *vbuf, *kalt, *valt;
+    int *rtmp;
+    JV_TRY(tmp.get(&perm, n));
+    JV_TRY(tmp.get(&iperm, n));
+    JV_TRY(tmp.get(&browptr, n + 1));
+    JV_TRY(tmp.get(&len, n));
+    JV_TRY(tmp.get(&bcolidx, nnz));
+    JV_TRY(tmp.get(&vmap, nnz));
+    JV_TRY(tmp.get(&src, nnz));
+    JV_TRY(tmp.get(&bcol, nnz));
+    JV_TRY(tmp.get(&brow, nnz));
+    JV_TRY(tmp.get(&kbuf, nnz));
+    JV_TRY(tmp.get(&vbuf, nnz));
+    JV_TRY(tmp.get(&kalt, nnz));
+    JV_TRY(tmp.get(&valt, nnz));
+    int m = std::max(n, nnz);
+    JV_TRY(tmp.get(&rtmp, radix_tmp_ints(m) + scan_tmp_ints(n)));
+    JV_CUDA(cudaMemcpyAsync(perm, h->ls[JV_LOWER].rows, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    count_launch();
+    k_inverse_perm<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, perm, iperm);
+    JV_CHECK_LAUNCH();
+    count_launch();
+    k_perm_lengths<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, perm, len);
+    JV_CHECK_LAUNCH();
+    JV_TRY(exclusive_scan_i32(len, browptr, n, rtmp, s));
+    count_launch();
+    k_perm_entries<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, h->colidx, perm, iperm,
+                                                          browptr, bcol, brow, src);
+    JV_CHECK_LAUNCH();
+    // sort by (row, col): stable by column first, then stable by row
+    JV_CUDA(cudaMemcpyAsync(kbuf, bcol, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+    JV_TRY(iota_i32((int *)vbuf, nnz, s));
+    JV_TRY(radix_sort_pairs(kbuf, vbuf, kalt, valt, nnz, bits_for(n - 1), rtmp, s));
+    count_launch();
+    k_gather_u32<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, brow, vbuf, kbuf);
+    JV_CHECK_LAUNCH();
+    JV_TRY(radix_sort_pairs(kbuf, vbuf, kalt, valt, nnz, bits_for(n - 1), rtmp, s));
+    count_launch();
+    k_perm_finish<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, vbuf, bcol, src, bcolidx, vmap);
+    JV_CHECK_LAUNCH();
+    JV_CUDA(cudaStreamSynchronize(s));
+
+    // rebuild every structure on B; keep perm / iperm / vmap
+    free_all(h);
+    JV_TRY(build_all(h, browptr, bcolidx));
+    JV_TRY(halloc_n(h, &h->perm, n));
+    JV_TRY(halloc_n(h, &h->iperm, n));
+    JV_TRY(halloc_n(h, &h->vmap, nnz));
+    JV_CUDA(cudaMemcpyAsync(h->perm, perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(h->iperm, iperm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(h->vmap, vmap, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    return JV_OK;
+}
+
+}  // namespace jv

@@ -1,0 +1,322 @@
+// extern "C" entry points declared in include/jv.h: argument checks, the
+// handle's life cycle and the status protocol.  All arithmetic is in the
+// kernels of the other translation units.
+#include <cstring>
+
+#include "jv_internal.cuh"
+
+namespace jv {
+void free_all(jv_handle h);
+}
+
+namespace {
+
+thread_local int t_last_bad_row = -1;
+
+size_t dtype_size(jv_dtype t) { return t == JV_F64 ? 8 : (t == JV_F32 ? 4 : 0); }
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+// After work has been enqueued: in check mode synchronise, read the device
+// status word, clear it and return it.
+int finish(jv_handle h, int rc, int *bad_row = nullptr) {
+    if (bad_row) *bad_row = -1;
+    if (rc != JV_OK) return rc;
+    if (!h->opt.check) return JV_OK;
+    JV_CUDA(cudaMemcpyAsync(h->h_status, h->status, 8, cudaMemcpyDeviceToHost, h->stream));
+    JV_CUDA(cudaStreamSynchronize(h->stream));
+    const unsigned long long key = *h->h_status;
+    if (key != ~0ull) JV_CUDA(cudaMemsetAsync(h->status, 0xff, 8, h->stream));
+    int row = -1;
+    int st = jv::decode_status(key, &row);
+    if (bad_row) *bad_row = row;
+    return st;
+}
+
+int enter(jv_handle h) {
+    if (!h) return JV_ERR_ARG;
+    JV_CUDA(cudaSetDevice(h->device));
+    return JV_OK;
+}
+
+void destroy_handle(jv_handle h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    jv::free_workspace(h);
+    jv::free_all(h);
+    if (h->flags) cudaFree(h->flags);
+    if (h->ticket) cudaFree(h->ticket);
+    if (h->status) cudaFree(h->status);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    cudaSetDevice(cur);
+    delete h;
+}
+
+int solve_common(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+                 const void *b, jv_dtype x_t, void *x, int nrhs) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!lu || !b || !x || nrhs < 1) return JV_ERR_ARG;
+    if (!dtype_size(lu_t) || !dtype_size(b_t) || !dtype_size(x_t)) return JV_ERR_ARG;
+    const size_t nb = (size_t)h->n * nrhs;
+    if (overlaps(b, nb * dtype_size(b_t), x, nb * dtype_size(x_t))) return JV_ERR_ARG;
+    if (overlaps(lu, (size_t)h->nnz * dtype_size(lu_t), x, nb * dtype_size(x_t))) return JV_ERR_ARG;
+    return finish(h, jv::tri_solve(h, structure, lu_t, lu, b_t, b, x_t, x, nrhs));
+}
+
+}  // namespace
+
+extern "C" {
+
+void jv_default_options(jv_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->mode = JV_MODE_SYNCFREE;
+    opt->reorder = 0;
+    opt->check = 1;
+    opt->vw_lower = 0;
+    opt->vw_upper = 0;
+    opt->spin_timeout_cycles = 0;
+    opt->fault_row = -1;
+}
+
+void jv_default_krylov_opts(jv_krylov_opts *o) {
+    if (!o) return;
+    o->tol = 1e-8;
+    o->maxit = 10000;
+    o->restart = 30;
+    o->max_restarts = 200;
+}
+
+int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx, const jv_options *opt,
+               void *stream, jv_handle *out) {
+    t_last_bad_row = -1;
+    if (!out) return JV_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || nnz < n || !rowptr || !colidx) return JV_ERR_ARG;
+    jv_handle h = new jv_handle_s();
+    if (opt) h->opt = *opt; else jv_default_options(&h->opt);
+    if (h->opt.mode != JV_MODE_LEVEL && h->opt.mode != JV_MODE_SYNCFREE) { delete h; return JV_ERR_ARG; }
+    for (int v : {h->opt.vw_lower, h->opt.vw_upper})
+        if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16 && v != 32) { delete h; return JV_ERR_ARG; }
+    h->n = n;
+    h->nnz = nnz;
+    h->stream = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return JV_ERR_CUDA; }
+    if (cudaMalloc(&h->flags, (size_t)n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->ticket, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&h->status, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&h->h_status, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_handle(h);
+        return JV_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->status, 0xff, 8, h->stream) != cudaSuccess) {
+        destroy_handle(h);
+        return JV_ERR_CUDA;
+    }
+    int rc = jv::analyze(h, rowptr, colidx);
+    if (rc == JV_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = JV_ERR_CUDA;
+    if (rc == JV_OK && cudaMemsetAsync(h->status, 0xff, 8, h->stream) != cudaSuccess) rc = JV_ERR_CUDA;
+    if (rc != JV_OK) {
+        t_last_bad_row = h->bad_row;
+        destroy_handle(h);
+        return rc;
+    }
+    *out = h;
+    return JV_OK;
+}
+
+int jv_last_bad_row(void) { return t_last_bad_row; }
+
+void jv_destroy(jv_handle h) { destroy_handle(h); }
+
+int jv_set_stream(jv_handle h, void *stream) {
+    if (!h) return JV_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return JV_OK;
+}
+
+int jv_set_mode(jv_handle h, int mode) {
+    if (!h || (mode != JV_MODE_LEVEL && mode != JV_MODE_SYNCFREE)) return JV_ERR_ARG;
+    h->opt.mode = mode;
+    return JV_OK;
+}
+
+int jv_set_check(jv_handle h, int check) {
+    if (!h) return JV_ERR_ARG;
+    h->opt.check = check ? 1 : 0;
+    return JV_OK;
+}
+
+int jv_ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu,
+                   int *bad_row) {
+    if (bad_row) *bad_row = -1;
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!vals || !lu || !dtype_size(vals_t) || !dtype_size(lu_t)) return JV_ERR_ARG;
+    if (vals == lu && vals_t != lu_t) return JV_ERR_ARG;
+    if (vals != lu && overlaps(vals, (size_t)h->nnz * dtype_size(vals_t), lu,
+                               (size_t)h->nnz * dtype_size(lu_t)))
+        return JV_ERR_ARG;
+    return finish(h, jv::ilu0_factor(h, vals_t, vals, lu_t, lu), bad_row);
+}
+
+int jv_lsolve(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t, const void *b,
+              jv_dtype x_t, void *x, int nrhs) {
+    return solve_common(h, JV_LOWER, lu_t, lu, b_t, b, x_t, x, nrhs);
+}
+int jv_usolve(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t, const void *b,
+              jv_dtype x_t, void *x, int nrhs) {
+    return solve_common(h, JV_UPPER, lu_t, lu, b_t, b, x_t, x, nrhs);
+}
+int jv_lsolve_t(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t, const void *b,
+                jv_dtype x_t, void *x, int nrhs) {
+    return solve_common(h, JV_LOWER_T, lu_t, lu, b_t, b, x_t, x, nrhs);
+}
+int jv_usolve_t(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t, const void *b,
+                jv_dtype x_t, void *x, int nrhs) {
+    return solve_common(h, JV_UPPER_T, lu_t, lu, b_t, b, x_t, x, nrhs);
+}
+
+int jv_spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, double alpha,
+            double beta) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!vals || !x || !y || !dtype_size(t)) return JV_ERR_ARG;
+    if (overlaps(x, (size_t)h->n * dtype_size(t), y, (size_t)h->n * dtype_size(t))) return JV_ERR_ARG;
+    return finish(h, jv::spmv(h, t, vals, x, y, alpha, beta));
+}
+
+int jv_masked_outer(jv_handle h, jv_dtype t, int which, const void *a, const void *b, int nrhs,
+                    double alpha, void *g) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!a || !b || !g || nrhs < 1 || !dtype_size(t) || (which != 0 && which != 1)) return JV_ERR_ARG;
+    return finish(h, jv::masked_outer(h, t, which, a, b, nrhs, alpha, g));
+}
+
+int jv_permute_values(jv_handle h, jv_dtype t, const void *in, void *out) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!h->vmap || !in || !out || in == out || !dtype_size(t)) return JV_ERR_ARG;
+    return finish(h, jv::permute_values(h, t, in, out));
+}
+
+int jv_permute_vector(jv_handle h, jv_dtype t, int inverse, const void *in, void *out, int nrhs) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!h->perm || !in || !out || in == out || nrhs < 1 || !dtype_size(t)) return JV_ERR_ARG;
+    return finish(h, jv::permute_vector(h, t, inverse ? 1 : 0, in, out, nrhs));
+}
+
+int jv_get_info(jv_handle h, jv_info *info) {
+    if (!h || !info) return JV_ERR_ARG;
+    info->n = h->n;
+    info->nnz = h->nnz;
+    info->nnz_lower = h->nnz_lower;
+    info->nnz_upper = h->nnz_upper;
+    for (int k = 0; k < 4; ++k) {
+        info->nlev[k] = h->ls[k].nlev;
+        info->vw[k] = h->ls[k].vw;
+    }
+    info->mode = h->opt.mode;
+    info->reorder = h->opt.reorder;
+    return JV_OK;
+}
+
+int jv_get_levels(jv_handle h, int which, int *nlev, const int **level_ptr,
+                  const int **level_rows, const int **lev) {
+    if (!h || which < 0 || which > 3) return JV_ERR_ARG;
+    const jv::LevelSet &L = h->ls[which];
+    if (nlev) *nlev = L.nlev;
+    if (level_ptr) *level_ptr = L.ptr;
+    if (level_rows) *level_rows = L.rows;
+    if (lev) *lev = L.lev;
+    return JV_OK;
+}
+
+int jv_get_pattern(jv_handle h, const int **rowptr, const int **colidx, const int **diag_ptr) {
+    if (!h) return JV_ERR_ARG;
+    if (rowptr) *rowptr = h->rowptr;
+    if (colidx) *colidx = h->colidx;
+    if (diag_ptr) *diag_ptr = h->diag;
+    return JV_OK;
+}
+
+int jv_get_csc(jv_handle h, const int **colptr, const int **rowidx, const int **csc2csr,
+               const int **cdiag) {
+    if (!h) return JV_ERR_ARG;
+    if (colptr) *colptr = h->colptr;
+    if (rowidx) *rowidx = h->rowidx;
+    if (csc2csr) *csc2csr = h->csc2csr;
+    if (cdiag) *cdiag = h->cdiag;
+    return JV_OK;
+}
+
+int jv_get_perm(jv_handle h, const int **perm, const int **iperm, const int **vmap) {
+    if (!h) return JV_ERR_ARG;
+    if (perm) *perm = h->perm;
+    if (iperm) *iperm = h->iperm;
+    if (vmap) *vmap = h->vmap;
+    return JV_OK;
+}
+
+int jv_status_sync(jv_handle h, int *bad_row) {
+    if (bad_row) *bad_row = -1;
+    int rc = enter(h);
+    if (rc) return rc;
+    JV_CUDA(cudaMemcpyAsync(h->h_status, h->status, 8, cudaMemcpyDeviceToHost, h->stream));
+    JV_CUDA(cudaStreamSynchronize(h->stream));
+    const unsigned long long key = *h->h_status;
+    JV_CUDA(cudaMemsetAsync(h->status, 0xff, 8, h->stream));
+    JV_CUDA(cudaStreamSynchronize(h->stream));
+    return jv::decode_status(key, bad_row);
+}
+
+int jv_pcg(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu, const double *b,
+           double *x, const jv_krylov_opts *o, jv_krylov_info *info) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!vals || !lu || !b || !x || !dtype_size(lu_t)) return JV_ERR_ARG;
+    jv_krylov_opts d;
+    jv_default_krylov_opts(&d);
+    return jv::pcg(h, vals, lu_t, lu, b, x, o ? o : &d, info);
+}
+
+int jv_fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu, const double *b,
+              double *x, const jv_krylov_opts *o, jv_krylov_info *info) {
+    int rc = enter(h);
+    if (rc) return rc;
+    if (!vals || !lu || !b || !x || !dtype_size(lu_t)) return JV_ERR_ARG;
+    jv_krylov_opts d;
+    jv_default_krylov_opts(&d);
+    return jv::fgmres(h, vals, lu_t, lu, b, x, o ? o : &d, info);
+}
+
+unsigned long long jv_launch_count(void) { return jv::g_launches.load(); }
+
+const char *jv_status_string(int status) {
+    switch (status) {
+        case JV_OK: return "ok";
+        case JV_ERR_ARG: return "invalid argument";
+        case JV_ERR_PATTERN: return "invalid sparsity pattern (index out of range, unsorted or duplicate column, or bad row pointer)";
+        case JV_ERR_NO_DIAG: return "a row has no stored diagonal entry";
+        case JV_ERR_ZERO_PIVOT: return "zero or non-finite pivot";
+        case JV_ERR_TIMEOUT: return "a sync-free wait timed out";
+        case JV_ERR_CUDA: return "CUDA runtime error";
+        case JV_ERR_NOMEM: return "device allocation failed";
+        case JV_ERR_INTERNAL: return "internal analysis error";
+        case JV_ERR_NOT_CONVERGED: return "Krylov iteration did not converge";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

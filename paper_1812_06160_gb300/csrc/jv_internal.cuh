@@ -1,0 +1,245 @@
+// Internal declarations of libjavelin_gb (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "jv.h"
+
+namespace jv {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;              // threads per CTA for every kernel here
+constexpr int kWarpsPerBlock = kBlock / kWarp;
+constexpr long long kDefaultSpin = 1ll << 32;
+
+// ---------------------------------------------------------------- launches
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+#define JV_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            std::fprintf(stderr, "libjavelin_gb: %s failed: %s (%s:%d)\n", \
+                         #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return JV_ERR_CUDA;                                         \
+        }                                                               \
+    } while (0)
+
+#define JV_CHECK_LAUNCH()                                               \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) {                                        \
+            std::fprintf(stderr, "libjavelin_gb: launch failed: %s (%s:%d)\n", \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);   \
+            return JV_ERR_CUDA;                                         \
+        }                                                               \
+    } while (0)
+
+inline int grid_for(long long work, int per_block) {
+    long long g = (work + per_block - 1) / per_block;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// ------------------------------------------------------------- device status
+// One 64-bit word per handle: min over reported errors of (row << 32 | -code),
+// so the smallest failing row wins and the word reads ~0 when all is well.
+__device__ __forceinline__ void report(unsigned long long *st, int code, int row) {
+    unsigned long long key = ((unsigned long long)(unsigned)row << 32) | (unsigned)(-code);
+    atomicMin(st, key);
+}
+inline int decode_status(unsigned long long key, int *row) {
+    if (key == ~0ull) { if (row) *row = -1; return JV_OK; }
+    if (row) *row = (int)(key >> 32);
+    return -(int)(key & 0xffffffffu);
+}
+
+// ------------------------------------------------------ memory-order helpers
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return __longlong_as_double((long long)v);
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ------------------------------------------------------ sync-free launches
+// Three words per handle: [0] next CTA ticket, [1] finished CTAs, [2] abort.
+// CTAs take tickets in launch order, so every task a CTA waits on belongs to
+// a CTA that is already running (or done): no wait can depend on a CTA that
+// is not resident.  The last CTA to finish resets all three words, so the
+// next launch starts from zero without a memset.  A wait that exceeds its
+// cycle budget reports JV_ERR_TIMEOUT and raises the abort word; every other
+// wait polls it and gives up too, so a fault costs one timeout period.
+__device__ __forceinline__ int sf_take_ticket(unsigned *ticket) {
+    __shared__ unsigned s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    return (int)s_ticket;
+}
+__device__ __forceinline__ void sf_finish(unsigned *ticket) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(ticket + 1, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(ticket, 0u);
+            atomicExch(ticket + 1, 0u);
+            atomicExch(ticket + 2, 0u);
+        }
+    }
+}
+__device__ __forceinline__ bool sf_aborted(const unsigned *ticket) {
+    return ld_relaxed(ticket + 2) != 0u;
+}
+__device__ __forceinline__ void sf_abort(unsigned *ticket) { atomicExch(ticket + 2, 1u); }
+
+// ---------------------------------------------------------------- sentinels
+// In sync-free solves the output vector itself carries readiness: it is
+// first filled with an all-ones bit pattern (a NaN payload that no
+// arithmetic result can carry, because results that are NaN are rewritten
+// to the canonical quiet NaN before they are stored), and a dependant spins
+// until the word it needs differs from it.  One aligned store publishes both
+// the value and its readiness, so no fence is needed on either side.
+template <class T> struct Bits;
+template <> struct Bits<double> {
+    using U = unsigned long long;
+    static constexpr U kSent = ~0ull;
+    static constexpr U kCanonNan = 0x7ff8000000000000ull;
+    __device__ static double from(U u) { return __longlong_as_double((long long)u); }
+    __device__ static U to(double d) { return (U)__double_as_longlong(d); }
+};
+template <> struct Bits<float> {
+    using U = unsigned;
+    static constexpr U kSent = ~0u;
+    static constexpr U kCanonNan = 0x7fc00000u;
+    __device__ static float from(U u) { return __uint_as_float(u); }
+    __device__ static U to(float f) { return __float_as_uint(f); }
+};
+
+// f(i) = a[i + ai] + ad: one kernel can walk a CSR or CSC sub-range of row or
+// column i (e.g. the strictly lower part of row i is [rowptr[i], diag[i])).
+struct Span {
+    const int *a;
+    int ai, ad;
+    __device__ __forceinline__ int at(int i) const { return __ldg(a + i + ai) + ad; }
+};
+
+// -------------------------------------------------------------- level sets
+struct LevelSet {
+    int nlev = 0;
+    int *lev = nullptr;        // [n] level of every row
+    int *ptr = nullptr;        // [nlev+1]
+    int *rows = nullptr;       // [n] rows grouped by level, ascending inside
+    std::vector<int> h_ptr;    // host copy of ptr
+    int vw = 1;                // lanes per row for the single-RHS kernels
+    int rows_per_task = 32;    // 32 / vw
+    int ntasks = 0;
+    int *task_lo = nullptr;    // [ntasks] positions in rows[]; a task never spans two levels
+    int *task_hi = nullptr;
+    std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
+};
+
+struct Workspace;  // Krylov scratch, krylov.cu
+
+}  // namespace jv
+
+struct jv_handle_s {
+    int device = 0;
+    int n = 0, nnz = 0;
+    int nnz_lower = 0, nnz_upper = 0;
+    cudaStream_t stream = nullptr;
+    jv_options opt{};
+    // pattern (B = P A P^T when reordering)
+    int *rowptr = nullptr, *colidx = nullptr, *diag = nullptr;
+    // CSC of the pattern
+    int *colptr = nullptr, *rowidx = nullptr, *csc2csr = nullptr, *cdiag = nullptr;
+    jv::LevelSet ls[4];
+    // reordering
+    int *perm = nullptr, *iperm = nullptr, *vmap = nullptr;
+    // scratch shared by the sync-free kernels
+    int *flags = nullptr;                    // [n] per-row "factored" flags
+    unsigned *ticket = nullptr;              // [2]: next CTA ticket, finished CTAs
+    unsigned long long *status = nullptr;    // device status word
+    unsigned long long *h_status = nullptr;  // pinned host mirror
+    int spmv_vw = 8;
+    int bad_row = -1;                        // row of the last analysis error
+    jv::Workspace *ws = nullptr;
+    std::vector<void *> allocs;              // everything to cudaFree on destroy
+};
+
+namespace jv {
+
+// allocation owned by the handle
+int halloc(jv_handle h, void **p, size_t bytes);
+template <class T> int halloc_n(jv_handle h, T **p, size_t count) {
+    return halloc(h, (void **)p, count * sizeof(T) + 16);
+}
+
+// prims.cu
+int fill_u32(void *p, size_t count_u32, unsigned v, cudaStream_t s);
+int iota_i32(int *p, int n, cudaStream_t s);
+// exclusive scan of in[0..m) into out[0..m]; out[m] = total.  tmp: >= scan_tmp_ints(m)
+size_t scan_tmp_ints(int m);
+int exclusive_scan_i32(const int *in, int *out, int m, int *tmp, cudaStream_t s);
+// stable LSD radix sort of (key, val) pairs by the low `bits` bits of key.
+// Sorts keys/vals in place (using the alt buffers); tmp >= radix_tmp_ints(m).
+size_t radix_tmp_ints(int m);
+int radix_sort_pairs(unsigned *keys, unsigned *vals, unsigned *keys_alt, unsigned *vals_alt,
+                     int m, int bits, int *tmp, cudaStream_t s);
+// ptr[k] = first position whose sorted key is >= k, k = 0..K (ptr[K] = m)
+int keys_to_ptr(const unsigned *sorted_keys, int m, int *ptr, int K, cudaStream_t s);
+
+// analyze.cu
+int analyze(jv_handle h, const int *rowptr, const int *colidx);
+
+// factor.cu
+int ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu);
+
+// trisolve.cu
+int tri_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+              const void *b, jv_dtype x_t, void *x, int nrhs);
+
+// spmv.cu
+int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, double alpha,
+         double beta);
+int masked_outer(jv_handle h, jv_dtype t, int which, const void *a, const void *b, int nrhs,
+                 double alpha, void *g);
+int permute_values(jv_handle h, jv_dtype t, const void *in, void *out);
+int permute_vector(jv_handle h, jv_dtype t, int inverse, const void *in, void *out, int nrhs);
+
+// krylov.cu
+int pcg(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu, const double *b,
+        double *x, const jv_krylov_opts *o, jv_krylov_info *info);
+int fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu, const double *b,
+           double *x, const jv_krylov_opts *o, jv_krylov_info *info);
+void free_workspace(jv_handle h);
+
+}  // namespace jv

@@ -1,0 +1,75 @@
+"""Shared helpers for the GPU parity tests (no arithmetic of the method here)."""
+import numpy as np
+
+import workloads as W
+
+
+def close(got, want, rel=1e-12, floor_frac=1e-6):
+    """Per-entry bound |g - o| <= rel * max(|o|, floor_frac * max|o|): relative
+    error per entry, with a floor for entries that cancelled to near zero
+    (the floor scale is the largest magnitude of the reference)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    scale = np.maximum(np.abs(want), floor_frac * (np.abs(want).max() if want.size else 0.0))
+    err = np.abs(got - want)
+    bad = err > rel * scale
+    return not bad.any(), float((err / np.where(scale > 0, scale, 1.0)).max() if want.size else 0.0)
+
+
+def max_rel(got, want):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    return float(np.abs(got - want).max() / max(np.abs(want).max(), 1e-300))
+
+
+def tridiag(n, d=4.0, o=-1.0):
+    rp = np.zeros(n + 1, dtype=np.int32)
+    cols, vals = [], []
+    for i in range(n):
+        for j, v in ((i - 1, o), (i, d), (i + 1, o)):
+            if 0 <= j < n:
+                cols.append(j)
+                vals.append(v)
+        rp[i + 1] = len(cols)
+    return rp, np.array(cols, dtype=np.int32), np.array(vals)
+
+
+def dense_lower(n, seed=0):
+    """Full lower triangle + diagonal + a superdiagonal: every row depends on all before it."""
+    rng = np.random.default_rng(seed)
+    rp = [0]
+    cols, vals = [], []
+    for i in range(n):
+        for j in range(0, min(i + 2, n)):
+            cols.append(j)
+            vals.append(rng.uniform(-1, 1) if j != i else float(n + 1))
+        rp.append(len(cols))
+    return np.array(rp, dtype=np.int32), np.array(cols, dtype=np.int32), np.array(vals)
+
+
+def small_matrices():
+    """(name, rowptr, colidx, vals): small cases that span several tiles,
+    ragged tails, long chains and degenerate shapes."""
+    out = []
+    for seed, (n, k, sym) in enumerate([(1, 0, False), (2, 1, False), (37, 3.0, False),
+                                        (250, 4.0, True), (600, 6.0, False), (1500, 2.5, False)]):
+        rp, ci, v = W.random_csr(n, k, seed=40 + seed, symmetric_pattern=sym)
+        out.append((f"rand{n}", rp, ci, v))
+    rp, ci, v = tridiag(3000)
+    out.append(("tridiag3000", rp, ci, v))
+    rp, ci, v = dense_lower(90, seed=3)
+    out.append(("denselower90", rp, ci, v))
+    n = 700
+    out.append(("diagonal700", np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32),
+                np.linspace(1.0, 2.0, n)))
+    rp, ci, v = W.lap5(33)
+    out.append(("lap5_33", rp, ci, v))
+    rp, ci, v = W.lap7(13)
+    out.append(("lap7_13", rp, ci, v))
+    rp, ci, v, _ = W.cd27(7)
+    out.append(("cd27_7", rp, ci, v))
+    rp, ci, v = W.aniso5(41)
+    out.append(("aniso5_41", rp, ci, v))
+    rp, ci, v = W.powerlaw(6000, kmax=400, seed_pattern=11, seed_values=12)
+    out.append(("powerlaw6000", rp, ci, v))
+    return out

@@ -1,0 +1,92 @@
+"""Failure paths on the GPU, none of which faults, traps or hangs it:
+zero pivots are reported with the oracle's row; a row that never publishes
+(test-only fault_row option) makes its dependants' bounded waits expire with
+JV_ERR_TIMEOUT, the launch completes and the context stays usable; argument
+errors are caught on the host before any launch."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+jv = pytest.importorskip("paper_1812_06160_gb300")
+pytestmark = pytest.mark.gpu
+
+
+def T(a):
+    return torch.tensor(np.asarray(a), device="cuda")
+
+
+@pytest.mark.parametrize("mode", ["level", "syncfree"])
+def test_zero_pivot_row_matches_oracle(mode):
+    rp = np.array([0, 2, 5, 7], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1, 2, 1, 2], dtype=np.int32)
+    v = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 3.0])
+    _, st, bad = O.ilu0(rp, ci, v)
+    assert st == O.ERR_ZERO_PIVOT and bad == 1
+    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_ilu0_factor(h, T(v))
+    assert e.value.status == jv.JV_ERR_ZERO_PIVOT and e.value.bad_row == 1
+
+
+def test_zero_pivot_in_large_matrix():
+    rp, ci, v = W.lap5(40)
+    diag = O.diag_ptr(rp, ci)
+    v2 = v.copy()
+    v2[rp[777]:diag[777] + 1] = 0.0          # no multipliers and a zero diagonal: u_777 == 0
+    _, st2, bad2 = O.ilu0(rp, ci, v2)
+    assert st2 == O.ERR_ZERO_PIVOT and bad2 == 777
+    for mode in ("level", "syncfree"):
+        h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+        with pytest.raises(jv.JvError) as e:
+            jv.jv_ilu0_factor(h, T(v2))
+        assert e.value.status == jv.JV_ERR_ZERO_PIVOT and e.value.bad_row == bad2
+
+
+def test_syncfree_timeout_is_reported_and_context_survives():
+    rp, ci, v = W.lap5(24)
+    n = len(rp) - 1
+    fault = 100
+    h = jv.jv_analyze(T(rp), T(ci), mode="syncfree", fault_row=fault,
+                      spin_timeout_cycles=2_000_000)
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_ilu0_factor(h, T(v))
+    assert e.value.status == jv.JV_ERR_TIMEOUT and e.value.bad_row > fault
+    olu, _, _ = O.ilu0(rp, ci, v)
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_lsolve(h, T(olu), T(W.rhs(n, 1, seed=1)))
+    assert e.value.status == jv.JV_ERR_TIMEOUT
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_lsolve(h, T(olu), T(W.rhs(n, 4, seed=1)))
+    assert e.value.status == jv.JV_ERR_TIMEOUT
+    # the device is still healthy: a clean handle factors bit-exactly
+    h2 = jv.jv_analyze(T(rp), T(ci), mode="syncfree")
+    assert np.array_equal(jv.jv_ilu0_factor(h2, T(v)).cpu().numpy(), olu)
+    torch.cuda.synchronize()
+
+
+def test_async_status_accumulates_until_sync():
+    rp = np.array([0, 2, 5, 7], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1, 2, 1, 2], dtype=np.int32)
+    v = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 3.0])
+    h = jv.jv_analyze(T(rp), T(ci), check=False)
+    jv.jv_ilu0_factor(h, T(v))               # enqueued, not checked
+    st, row = jv.jv_status_sync(h)
+    assert st == jv.JV_ERR_ZERO_PIVOT and row == 1
+    assert jv.jv_status_sync(h) == (0, -1)
+
+
+def test_host_argument_errors():
+    rp, ci, v = W.lap5(8)
+    h = jv.jv_analyze(T(rp), T(ci))
+    lu = jv.jv_ilu0_factor(h, T(v))
+    b = T(W.rhs(64, 1))
+    with pytest.raises(ValueError):
+        jv.jv_lsolve(h, lu, b[:10])
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_lsolve(h, lu, b, x=b)          # x aliases b
+    assert e.value.status == jv.JV_ERR_ARG
+    with pytest.raises(TypeError):
+        jv.jv_ilu0_factor(h, T(v).to(torch.int64))

@@ -1,0 +1,157 @@
+"""GPU factor / solves / spmv / masked outer product vs the oracle.
+
+Bars: the FP64 and FP32 factors are bit-exact (the kernel performs Fig. 1's
+operations in the oracle's order, each rounded separately); FP64 solves are
+within 1e-12 relative per entry (floor 1e-6 x max|x| for cancelled entries);
+spmv and the masked outer product within 1e-12 of the componentwise scale
+sum |a||b|; FP32 solves are reported against the FP64 oracle and bounded."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from jvutil import close, max_rel, small_matrices
+
+jv = pytest.importorskip("paper_1812_06160_gb300")
+pytestmark = pytest.mark.gpu
+
+CASES = small_matrices()
+IDS = [c[0] for c in CASES]
+MODES = ["level", "syncfree"]
+
+
+def T(a):
+    return torch.tensor(np.asarray(a), device="cuda")
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_factor_fp64_bit_exact(case, mode):
+    _, rp, ci, v = case
+    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    lu = jv.jv_ilu0_factor(h, T(v))
+    olu, st, _ = O.ilu0(rp, ci, v)
+    assert st == 0
+    assert np.array_equal(lu.cpu().numpy(), olu)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_factor_fp32_bit_exact_to_fp32_twin(case, mode):
+    _, rp, ci, v = case
+    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    olu32, st, _ = O.ilu0(rp, ci, v.astype(np.float32), dtype=np.float32)
+    lu = jv.jv_ilu0_factor(h, T(v), lu_dtype=torch.float32)        # fused down-cast
+    assert np.array_equal(lu.cpu().numpy(), olu32)
+    inplace = T(v.astype(np.float32))
+    jv.jv_ilu0_factor(h, inplace, lu=inplace)                        # in place
+    assert np.array_equal(inplace.cpu().numpy(), olu32)
+    olu64, _, _ = O.ilu0(rp, ci, v)
+    if len(v) > 1:
+        assert max_rel(olu32, olu64) < 1e-4     # reported FP32-vs-FP64 error, bounded
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("nrhs", [1, 3, 33])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solves_fp64(case, nrhs, mode):
+    _, rp, ci, v = case
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    olu, _, _ = O.ilu0(rp, ci, v)
+    diag = O.diag_ptr(rp, ci)
+    b = W.rhs(n, nrhs, seed=7 + nrhs)
+    lu = T(olu)
+    bt = T(b)
+    for name, ofn in (("jv_lsolve", O.lsolve), ("jv_usolve", O.usolve),
+                      ("jv_lsolve_t", O.lsolve_t), ("jv_usolve_t", O.usolve_t)):
+        x = getattr(jv, name)(h, lu, bt).cpu().numpy()
+        ok, err = close(x, ofn(rp, ci, diag, olu, b))
+        assert ok, (name, err)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solves_fp32_and_mixed(case, mode):
+    _, rp, ci, v = case
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    olu32, _, _ = O.ilu0(rp, ci, v.astype(np.float32), dtype=np.float32)
+    diag = O.diag_ptr(rp, ci)
+    lu64 = olu32.astype(np.float64)
+    b = W.rhs(n, 1, seed=5)
+    lu = T(olu32)
+    want_y = O.lsolve(rp, ci, diag, lu64, b)
+    want_z = O.usolve(rp, ci, diag, lu64, want_y)
+    y32 = jv.jv_lsolve(h, lu, T(b.astype(np.float32)))
+    assert y32.dtype == torch.float32 and max_rel(y32.cpu().numpy(), want_y) < 1e-4
+    ym = jv.jv_lsolve(h, lu, T(b))                                   # FP64 in, FP32 out
+    assert ym.dtype == torch.float32 and max_rel(ym.cpu().numpy(), want_y) < 1e-4
+    zm = jv.jv_usolve(h, lu, ym, x_dtype=torch.float64)              # FP32 in, FP64 out
+    assert zm.dtype == torch.float64 and max_rel(zm.cpu().numpy(), want_z) < 1e-4
+    b3 = W.rhs(n, 5, seed=6)
+    x3 = jv.jv_usolve_t(h, lu, T(b3.astype(np.float32))).cpu().numpy()
+    assert max_rel(x3, O.usolve_t(rp, ci, diag, lu64, b3)) < 1e-4
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_spmv(case):
+    _, rp, ci, v = case
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci))
+    x = W.rhs(n, 1, seed=3)
+    y0 = W.rhs(n, 1, seed=4)
+    scale = O.spmv(rp, ci, np.abs(v), np.abs(x)) + np.abs(y0)
+    for alpha, beta in ((1.0, 0.0), (-2.0, 0.5)):
+        y = jv.jv_spmv(h, T(v), T(x), T(y0), alpha=alpha, beta=beta).cpu().numpy()
+        want = O.spmv(rp, ci, v, x, y0, alpha=alpha, beta=beta)
+        assert np.all(np.abs(y - want) <= 1e-12 * 2 * scale)
+    y32 = jv.jv_spmv(h, T(v.astype(np.float32)), T(x.astype(np.float32))).cpu().numpy()
+    assert np.all(np.abs(y32 - O.spmv(rp, ci, v, x)) <= 1e-5 * (scale + 1e-30))
+
+
+@pytest.mark.parametrize("case", CASES[2:6], ids=IDS[2:6])
+def test_masked_outer(case):
+    _, rp, ci, _ = case
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci))
+    diag = O.diag_ptr(rp, ci)
+    a, b = W.rhs(n, 7, seed=1), W.rhs(n, 7, seed=2)
+    for which in (0, 1):
+        g = jv.jv_masked_outer(h, which, T(a), T(b), alpha=-1.0).cpu().numpy()
+        want = O.masked_outer(rp, ci, diag, which, a, b, alpha=-1.0)
+        scale = O.masked_outer(rp, ci, diag, which, np.abs(a), np.abs(b))
+        assert np.all(np.abs(g - want) <= 1e-12 * scale)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_reordered_factor_and_solve(case):
+    """B = P A P^T: the factor of B is bit-exact to the oracle's factor of B;
+    solving in B's order and permuting back matches the natural-order solve
+    (the level order keeps lower(A) lower on these symmetric-pattern cases,
+    up to summation order)."""
+    _, rp, ci, v = case
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci), reorder=True)
+    _, _, _, perm = O.level_sets(rp, ci)
+    iperm, brp, bci, vmap = O.permute(rp, ci, perm)
+    vb = jv.jv_permute_values(h, T(v))
+    assert np.array_equal(vb.cpu().numpy(), v[vmap])
+    lu = jv.jv_ilu0_factor(h, vb)
+    olu, _, _ = O.ilu0(brp, bci, v[vmap])
+    assert np.array_equal(lu.cpu().numpy(), olu)
+    b = W.rhs(n, 2, seed=9)
+    bb = jv.jv_permute_vector(h, T(b))
+    assert np.array_equal(bb.cpu().numpy(), b[perm])
+    z = jv.jv_usolve(h, lu, jv.jv_lsolve(h, lu, bb))
+    back = jv.jv_permute_vector(h, z, inverse=True).cpu().numpy()
+    bdiag = O.diag_ptr(brp, bci)
+    want_b = O.usolve(brp, bci, bdiag, olu, O.lsolve(brp, bci, bdiag, olu, b[perm]))
+    assert close(z.cpu().numpy(), want_b)[0]
+    sym = np.array_equal(O.transpose(rp, ci)[0], rp) and np.array_equal(O.transpose(rp, ci)[1], ci)
+    if sym:
+        olu_a, _, _ = O.ilu0(rp, ci, v)
+        diag = O.diag_ptr(rp, ci)
+        want = O.usolve(rp, ci, diag, olu_a, O.lsolve(rp, ci, diag, olu_a, b))
+        assert close(back, want, rel=1e-10)[0]
