@@ -14,8 +14,10 @@
  *   - L is unit lower triangular and stored strictly below the diagonal;
  *     U carries the diagonal; both live in A's own pattern (Fig. 1: "L and U
  *     are stored in A").
- *   - Every floating-point statement is a separate IEEE operation; the file
- *     is compiled with -ffp-contract=off so no multiply-add is fused.
+ *   - Every update of the form s <- s -/+ a*b is one fused multiply-add
+ *     (C99 fma / fmaf: the exact a*b added to s, rounded once); every other
+ *     statement is a separate IEEE operation (the file is compiled with
+ *     -ffp-contract=off, so nothing else is fused).
  *   - Multi-right-hand-side vectors are row-major n x nrhs.
  *
  * Status codes (numbers chosen to read the same as the library's, by
@@ -212,7 +214,8 @@ void jvo_permute(int n, const int *rowptr, const int *colidx, const int *perm,
 /* ILU(0), up-looking (row-wise left-looking, "IKJ") on A's own pattern --   */
 /* Sec. III, Fig. 1.  For every row i, for every col k < i of row i in       */
 /* ascending order: a_ik <- a_ik / a_kk, then for every update column j > k  */
-/* of row k that is also in row i: a_ij <- a_ij - a_ik * a_kj.  No pivoting  */
+/* of row k that is also in row i: a_ij <- a_ij - a_ik * a_kj (one fused     */
+/* multiply-add, rounded once).  No pivoting                                 */
 /* (Sec. III).  Membership of j in row i is found through a dense scatter of */
 /* row i.  A zero or non-finite pivot a_ii stops the factorisation with      */
 /* bad_row = i.  In place on a[].                                             */
@@ -232,8 +235,7 @@ int jvo_ilu0(int n, const int *rowptr, const int *colidx, const int *diag,
             for (int q = diag[k] + 1; q < rowptr[k + 1]; ++q) {
                 int j = colidx[q];
                 if (pos[j] >= 0) {
-                    double prod = lik * a[q];
-                    a[pos[j]] = a[pos[j]] - prod;
+                    a[pos[j]] = fma(-lik, a[q], a[pos[j]]);
                 }
             }
         }
@@ -267,8 +269,7 @@ int jvo_ilu0_f32(int n, const int *rowptr, const int *colidx, const int *diag,
             for (int q = diag[k] + 1; q < rowptr[k + 1]; ++q) {
                 int j = colidx[q];
                 if (pos[j] >= 0) {
-                    float prod = lik * a[q];
-                    a[pos[j]] = a[pos[j]] - prod;
+                    a[pos[j]] = fmaf(-lik, a[q], a[pos[j]]);
                 }
             }
         }
@@ -296,8 +297,7 @@ void jvo_lsolve(int n, const int *rowptr, const int *colidx, const int *diag,
         for (int c = 0; c < nrhs; ++c) {
             double s = b[(size_t)i * nrhs + c];
             for (int p = rowptr[i]; p < diag[i]; ++p) {
-                double prod = lu[p] * x[(size_t)colidx[p] * nrhs + c];
-                s = s - prod;
+                s = fma(-lu[p], x[(size_t)colidx[p] * nrhs + c], s);
             }
             x[(size_t)i * nrhs + c] = s;
         }
@@ -311,8 +311,7 @@ void jvo_usolve(int n, const int *rowptr, const int *colidx, const int *diag,
         for (int c = 0; c < nrhs; ++c) {
             double s = b[(size_t)i * nrhs + c];
             for (int p = diag[i] + 1; p < rowptr[i + 1]; ++p) {
-                double prod = lu[p] * x[(size_t)colidx[p] * nrhs + c];
-                s = s - prod;
+                s = fma(-lu[p], x[(size_t)colidx[p] * nrhs + c], s);
             }
             x[(size_t)i * nrhs + c] = s / lu[diag[i]];
         }
@@ -331,8 +330,8 @@ void jvo_usolve_t(int n, const int *rowptr, const int *colidx, const int *diag,
             double xi = g[(size_t)i * nrhs + c] / lu[diag[i]];
             x[(size_t)i * nrhs + c] = xi;
             for (int p = diag[i] + 1; p < rowptr[i + 1]; ++p) {
-                double prod = lu[p] * xi;
-                g[(size_t)colidx[p] * nrhs + c] = g[(size_t)colidx[p] * nrhs + c] - prod;
+                size_t o = (size_t)colidx[p] * nrhs + c;
+                g[o] = fma(-lu[p], xi, g[o]);
             }
         }
     free(g);
@@ -351,8 +350,8 @@ void jvo_lsolve_t(int n, const int *rowptr, const int *colidx, const int *diag,
             double xi = g[(size_t)i * nrhs + c];
             x[(size_t)i * nrhs + c] = xi;
             for (int p = rowptr[i]; p < diag[i]; ++p) {
-                double prod = lu[p] * xi;
-                g[(size_t)colidx[p] * nrhs + c] = g[(size_t)colidx[p] * nrhs + c] - prod;
+                size_t o = (size_t)colidx[p] * nrhs + c;
+                g[o] = fma(-lu[p], xi, g[o]);
             }
         }
     free(g);
@@ -373,8 +372,7 @@ void jvo_masked_outer(int n, const int *rowptr, const int *colidx,
             int j = colidx[p];
             double s = 0.0;
             for (int c = 0; c < nrhs; ++c) {
-                double prod = a[(size_t)i * nrhs + c] * b[(size_t)j * nrhs + c];
-                s = s + prod;
+                s = fma(a[(size_t)i * nrhs + c], b[(size_t)j * nrhs + c], s);
             }
             g[p] = alpha * s;
         }
@@ -391,8 +389,7 @@ void jvo_spmv(int n, const int *rowptr, const int *colidx, const double *a,
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
         for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-            double prod = a[p] * x[colidx[p]];
-            s = s + prod;
+            s = fma(a[p], x[colidx[p]], s);
         }
         double v = alpha * s;
         if (beta != 0.0) v = v + beta * y[i];
