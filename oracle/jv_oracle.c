@@ -392,7 +392,7 @@ void jvo_spmv(int n, const int *rowptr, const int *colidx, const double *a,
             s = fma(a[p], x[colidx[p]], s);
         }
         double v = alpha * s;
-        if (beta != 0.0) v = v + beta * y[i];
+        if (beta != 0.0) v = fma(beta, y[i], v);
         y[i] = v;
     }
 }
