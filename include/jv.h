@@ -73,18 +73,27 @@ typedef struct {
                                        ordering); every vector and value array passed to
                                        the handle is then in B's order.  Default 0. */
     int check;                      /* 1 (default): synchronise and return device status */
-    int vw_lower;                   /* lanes per row for LOWER/UPPER_T kernels; 0 = auto */
-    int vw_upper;                   /* lanes per row for UPPER/LOWER_T kernels; 0 = auto */
+    int long_row;                   /* solve rows with more dependencies than this run one
+                                       row per warp (lanes cooperate); shorter rows run one
+                                       row per lane, 32 to a warp.  0 = default (24) */
     long long spin_timeout_cycles;  /* bound on every sync-free wait; 0 = default (2^32) */
     int fault_row;                  /* TEST ONLY: this row never publishes its result, so
                                        its dependants time out.  -1 (default) = off. */
+    int sf_ctas_per_sm;             /* sync-free launches run a persistent grid of this many
+                                       CTAs per SM (bounds how many rows poll at once);
+                                       0 = default */
+    int sf_backoff_ns;              /* longest pause between two polls of a value that is not
+                                       ready; 0 = default, negative = never pause */
 } jv_options;
 
 typedef struct {
     int n, nnz;
     int nnz_lower, nnz_upper;   /* strictly lower / strictly upper entries */
     int nlev[4];                /* levels per jv_structure */
-    int vw[4];                  /* lanes per row chosen per jv_structure */
+    int nlong[4];               /* rows run one per warp, per jv_structure */
+    int nlong_factor;           /* rows the factor runs one per warp */
+    long long npairs;           /* update pairs of the symbolic factorisation (flops of the
+                                   factor = 2 npairs + nnz_lower) */
     int mode, reorder;
 } jv_info;
 

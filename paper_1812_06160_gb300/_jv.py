@@ -36,14 +36,16 @@ STRUCTURES = {"L": JV_LOWER, "U": JV_UPPER, "Ut": JV_UPPER_T, "Lt": JV_LOWER_T}
 
 class jv_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("reorder", ctypes.c_int), ("check", ctypes.c_int),
-                ("vw_lower", ctypes.c_int), ("vw_upper", ctypes.c_int),
-                ("spin_timeout_cycles", ctypes.c_longlong), ("fault_row", ctypes.c_int)]
+                ("long_row", ctypes.c_int),
+                ("spin_timeout_cycles", ctypes.c_longlong), ("fault_row", ctypes.c_int),
+                ("sf_ctas_per_sm", ctypes.c_int), ("sf_backoff_ns", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_int), ("nnz_lower", ctypes.c_int),
-                ("nnz_upper", ctypes.c_int), ("nlev", ctypes.c_int * 4), ("vw", ctypes.c_int * 4),
-                ("mode", ctypes.c_int), ("reorder", ctypes.c_int)]
+                ("nnz_upper", ctypes.c_int), ("nlev", ctypes.c_int * 4),
+                ("nlong", ctypes.c_int * 4), ("nlong_factor", ctypes.c_int),
+                ("npairs", ctypes.c_longlong), ("mode", ctypes.c_int), ("reorder", ctypes.c_int)]
 
 
 class jv_krylov_opts(ctypes.Structure):
@@ -151,7 +153,7 @@ class _DevView:
     """Zero-copy view of a handle-owned int32 device array."""
 
     def __init__(self, ptr, n):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False),
                                          "version": 3, "strides": None}
 
 
@@ -179,8 +181,8 @@ class Handle:
         return jv_get_info(self)
 
 
-def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, vw_lower=0,
-               vw_upper=0, spin_timeout_cycles=0, fault_row=-1):
+def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_row=0,
+               spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0):
     """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle."""
     n = rowptr.numel() - 1
     nnz = colidx.numel()
@@ -191,10 +193,11 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, vw_lo
     opt.mode = {"level": JV_MODE_LEVEL, "syncfree": JV_MODE_SYNCFREE}[mode]
     opt.reorder = int(bool(reorder))
     opt.check = int(bool(check))
-    opt.vw_lower = int(vw_lower)
-    opt.vw_upper = int(vw_upper)
+    opt.long_row = int(long_row)
     opt.spin_timeout_cycles = int(spin_timeout_cycles)
     opt.fault_row = int(fault_row)
+    opt.sf_ctas_per_sm = int(sf_ctas_per_sm)
+    opt.sf_backoff_ns = int(sf_backoff_ns)
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):
@@ -315,7 +318,8 @@ def jv_get_info(h):
     info = jv_info()
     _check("jv_get_info", lib.jv_get_info(h.ptr, ctypes.byref(info)))
     return dict(n=info.n, nnz=info.nnz, nnz_lower=info.nnz_lower, nnz_upper=info.nnz_upper,
-                nlev=list(info.nlev), vw=list(info.vw), mode=info.mode, reorder=info.reorder)
+                nlev=list(info.nlev), nlong=list(info.nlong), nlong_factor=info.nlong_factor,
+                npairs=info.npairs, mode=info.mode, reorder=info.reorder)
 
 
 def jv_get_levels(h, which="L"):

@@ -117,6 +117,42 @@ __global__ void k_csc_finish(int nnz, const unsigned *col_sorted, const unsigned
     if ((unsigned)r == col_sorted[q]) cdiag[r] = q;
 }
 
+// -------------------------------------------------- symbolic factorisation
+// For the strictly lower entry p = (r, k) of row r, Fig. 1 updates every
+// a_rj with j > k, j in row k and in row r.  One warp per row, lanes over the
+// row's lower entries; the pairs (t = position of (r, j), q = position of
+// (k, j)) of one p are listed in ascending j, which is the order Fig. 1 applies
+// them.  Pass 1 counts (cnt[p], zero off the lower part), pass 2 fills.
+template <bool FILL>
+__global__ void k_pairs(int n, const int *rowptr, const int *colidx, const int *diag, int *cnt,
+                        const int *ptr, int2 *pairs) {
+    const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int rs = rowptr[r], re = rowptr[r + 1], rd = diag[r];
+    for (int p = rs + lane; p < rd; p += 32) {
+        const int k = colidx[p];
+        const int ke = rowptr[k + 1];
+        int c = 0;
+        const int base = FILL ? ptr[p] : 0;
+        for (int q = diag[k] + 1; q < ke; ++q) {
+            const int t = find_col(colidx, p + 1, re, colidx[q]);
+            if (t >= 0) {
+                if (FILL) pairs[base + c] = make_int2(t, q);
+                ++c;
+            }
+        }
+        if (!FILL) cnt[p] = c;
+    }
+    if (!FILL)
+        for (int p = rd + lane; p < re; p += 32) cnt[p] = 0;
+}
+
+__global__ void k_kdiag(int nnz, const int *colidx, const int *diag, int *kdiag) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) kdiag[p] = diag[colidx[p]];
+}
+
 // ---------------------------------------------------------------- peeling
 struct Dag {
     Span cnt_beg, cnt_end;   // number of dependencies of v = cnt_end(v) - cnt_beg(v)
@@ -198,14 +234,8 @@ int peel_levels(jv_handle h, const Dag &g, int *lev, Temp &tmp, int *nlev_out,
     }
 }
 
-int pow2_lanes(double mean) {
-    int v = 1;
-    while (v < 32 && v < mean) v <<= 1;
-    return v;
-}
-
-// Level sets of one DAG + the per-level task lists.
-int build_levelset(jv_handle h, int which, const Dag &g, int vw, Temp &tmp, unsigned *kbuf,
+// Level sets of one DAG: level of every row, rows grouped by level.
+int build_levelset(jv_handle h, int which, const Dag &g, Temp &tmp, unsigned *kbuf,
                    unsigned *vbuf, unsigned *kalt, unsigned *valt, int *rtmp) {
     const int n = h->n;
     cudaStream_t s = h->stream;
@@ -229,25 +259,61 @@ int build_levelset(jv_handle h, int which, const Dag &g, int vw, Temp &tmp, unsi
     JV_CUDA(cudaStreamSynchronize(s));
     for (int l = 0; l < L.nlev; ++l)
         if (L.h_ptr[l + 1] - L.h_ptr[l] != widths[l]) return JV_ERR_INTERNAL;
-    // tasks: up to R rows of one level
-    L.vw = vw;
-    L.rows_per_task = kWarp / vw;
-    const int R = L.rows_per_task;
-    std::vector<int> lo, hi;
-    L.h_task_ptr.assign(L.nlev + 1, 0);
+    return JV_OK;
+}
+
+// Per-row costs for the binning: dependencies of the four solves, and for
+// the factor the shared-memory words a row needs (its values plus every U
+// value it reads: one u_kk per lower entry and one u_kj per update pair).
+__global__ void k_row_costs(int n, const int *rowptr, const int *diag, const int *colptr,
+                            const int *cdiag, const int *pair_ptr, int *cost) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int rs = rowptr[i], re = rowptr[i + 1], rd = diag[i];
+    cost[i] = rd - rs;
+    cost[(size_t)n + i] = re - rd - 1;
+    cost[2 * (size_t)n + i] = cdiag[i] - colptr[i];
+    cost[3 * (size_t)n + i] = colptr[i + 1] - cdiag[i] - 1;
+    cost[4 * (size_t)n + i] = (re - rs) + (rd - rs) + (pair_ptr[rd] - pair_ptr[rs]);
+}
+
+// Host-side binning of one level structure (see Bins).
+int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, Bins &B) {
+    const int n = h->n;
+    cudaStream_t s = h->stream;
+    std::vector<int> rows((size_t)n), brows, lo, hi;
+    JV_CUDA(cudaMemcpyAsync(rows.data(), L.rows, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    brows.reserve(n);
+    B.h_task_ptr.assign(L.nlev + 1, 0);
+    B.nlong = 0;
     for (int l = 0; l < L.nlev; ++l) {
-        L.h_task_ptr[l] = (int)lo.size();
-        for (int a = L.h_ptr[l]; a < L.h_ptr[l + 1]; a += R) {
-            lo.push_back(a);
-            hi.push_back(std::min(a + R, L.h_ptr[l + 1]));
+        B.h_task_ptr[l] = (int)lo.size();
+        const int a = L.h_ptr[l], e = L.h_ptr[l + 1];
+        const int first = (int)brows.size();
+        for (int t = a; t < e; ++t)
+            if (cost[rows[t]] <= threshold) brows.push_back(rows[t]);
+        const int nshort = (int)brows.size() - first;
+        for (int t = 0; t < nshort; t += kWarp) {
+            lo.push_back(first + t);
+            hi.push_back(first + std::min(t + kWarp, nshort));
         }
+        for (int t = a; t < e; ++t)
+            if (cost[rows[t]] > threshold) {
+                lo.push_back((int)brows.size());
+                hi.push_back(((int)brows.size() + 1) | kLongBit);
+                brows.push_back(rows[t]);
+                ++B.nlong;
+            }
     }
-    L.ntasks = (int)lo.size();
-    L.h_task_ptr[L.nlev] = L.ntasks;
-    JV_TRY(halloc_n(h, &L.task_lo, L.ntasks));
-    JV_TRY(halloc_n(h, &L.task_hi, L.ntasks));
-    JV_CUDA(cudaMemcpyAsync(L.task_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s));
-    JV_CUDA(cudaMemcpyAsync(L.task_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s));
+    B.ntasks = (int)lo.size();
+    B.h_task_ptr[L.nlev] = B.ntasks;
+    JV_TRY(halloc_n(h, &B.rows, n));
+    JV_TRY(halloc_n(h, &B.task_lo, B.ntasks));
+    JV_TRY(halloc_n(h, &B.task_hi, B.ntasks));
+    JV_CUDA(cudaMemcpyAsync(B.rows, brows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(B.task_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(B.task_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
     return JV_OK;
 }
@@ -309,20 +375,69 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     JV_CHECK_LAUNCH();
 
     // the four DAGs
-    const double mean_l = (double)h->nnz_lower / n, mean_u = (double)h->nnz_upper / n;
-    int vwl = h->opt.vw_lower > 0 ? h->opt.vw_lower : pow2_lanes(mean_l);
-    int vwu = h->opt.vw_upper > 0 ? h->opt.vw_upper : pow2_lanes(mean_u);
     Dag gl{{h->rowptr, 0, 0}, {h->diag, 0, 0}, {h->cdiag, 0, 1}, {h->colptr, 1, 0}, h->rowidx};
     Dag gu{{h->diag, 0, 1}, {h->rowptr, 1, 0}, {h->colptr, 0, 0}, {h->cdiag, 0, 0}, h->rowidx};
     Dag gut{{h->colptr, 0, 0}, {h->cdiag, 0, 0}, {h->diag, 0, 1}, {h->rowptr, 1, 0}, h->colidx};
     Dag glt{{h->cdiag, 0, 1}, {h->colptr, 1, 0}, {h->rowptr, 0, 0}, {h->diag, 0, 0}, h->colidx};
-    JV_TRY(build_levelset(h, JV_LOWER, gl, vwl, tmp, kbuf, vbuf, kalt, valt, rtmp));
-    JV_TRY(build_levelset(h, JV_UPPER, gu, vwu, tmp, kbuf, vbuf, kalt, valt, rtmp));
-    JV_TRY(build_levelset(h, JV_UPPER_T, gut, vwu, tmp, kbuf, vbuf, kalt, valt, rtmp));
-    JV_TRY(build_levelset(h, JV_LOWER_T, glt, vwl, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_LOWER, gl, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_UPPER, gu, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_UPPER_T, gut, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    JV_TRY(build_levelset(h, JV_LOWER_T, glt, tmp, kbuf, vbuf, kalt, valt, rtmp));
 
-    double mean = (double)nnz / n;
-    h->spmv_vw = pow2_lanes(mean);
+    // symbolic factorisation: the update pairs of every strictly lower entry
+    int *cnt = (int *)kbuf;   // nnz counts (kbuf is free again)
+    JV_TRY(halloc_n(h, &h->pair_ptr, (size_t)nnz + 1));
+    count_launch();
+    k_pairs<false><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(n, h->rowptr, h->colidx, h->diag,
+                                                                  cnt, nullptr, nullptr);
+    JV_CHECK_LAUNCH();
+    JV_TRY(exclusive_scan_i32(cnt, h->pair_ptr, nnz, rtmp, s));
+    int np = 0;
+    JV_CUDA(cudaMemcpyAsync(&np, h->pair_ptr + nnz, 4, cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    h->npairs = np;
+    JV_TRY(halloc_n(h, &h->pairs, (size_t)np + 1));
+    count_launch();
+    k_pairs<true><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(n, h->rowptr, h->colidx, h->diag,
+                                                                 nullptr, h->pair_ptr, h->pairs);
+    JV_CHECK_LAUNCH();
+    JV_TRY(halloc_n(h, &h->kdiag, nnz));
+    count_launch();
+    k_kdiag<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, h->colidx, h->diag, h->kdiag);
+    JV_CHECK_LAUNCH();
+
+    // spmv row blocks (greedy over the host copy of rowptr) and the longest row
+    std::vector<int> hrp((size_t)n + 1);
+    JV_CUDA(cudaMemcpyAsync(hrp.data(), h->rowptr, hrp.size() * 4, cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> blk;
+    h->maxrow = 0;
+    for (int r = 0; r < n;) {
+        blk.push_back(r);
+        int e = r + 1;
+        while (e < n && e - r < kSpmvRows && hrp[e + 1] - hrp[r] <= kSpmvCap) ++e;
+        for (int i = r; i < e; ++i) h->maxrow = std::max(h->maxrow, hrp[i + 1] - hrp[i]);
+        r = e;
+    }
+    blk.push_back(n);
+    h->nspmv_blk = (int)blk.size() - 1;
+    JV_TRY(halloc_n(h, &h->spmv_blk, blk.size()));
+    JV_CUDA(cudaMemcpyAsync(h->spmv_blk, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice, s));
+
+    // binned work lists: the four solves and the factor
+    int *dcost;
+    JV_TRY(tmp.get(&dcost, 5 * (size_t)n));
+    count_launch();
+    k_row_costs<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, h->diag, h->colptr, h->cdiag,
+                                                       h->pair_ptr, dcost);
+    JV_CHECK_LAUNCH();
+    std::vector<int> cost(5 * (size_t)n);
+    JV_CUDA(cudaMemcpyAsync(cost.data(), dcost, cost.size() * 4, cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    const int long_deps = h->opt.long_row > 0 ? h->opt.long_row : kLongDeps;
+    for (int k = 0; k < 4; ++k)
+        JV_TRY(make_bins(h, h->ls[k], cost.data() + (size_t)k * n, long_deps, h->ls[k].bins));
+    JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, kLaneSlot, h->fbins));
     return JV_OK;
 }
 
@@ -367,6 +482,7 @@ void free_all(jv_handle h) {
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     for (auto &L : h->ls) L = LevelSet();
+    h->fbins = Bins();
 }
 
 int analyze(jv_handle h, const int *rowptr, const int *colidx) {

@@ -50,7 +50,7 @@ void destroy_handle(jv_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     jv::free_workspace(h);
     jv::free_all(h);
-    if (h->flags) cudaFree(h->flags);
+    if (h->fscratch) cudaFree(h->fscratch);
     if (h->ticket) cudaFree(h->ticket);
     if (h->status) cudaFree(h->status);
     if (h->h_status) cudaFreeHost(h->h_status);
@@ -80,10 +80,11 @@ void jv_default_options(jv_options *opt) {
     opt->mode = JV_MODE_SYNCFREE;
     opt->reorder = 0;
     opt->check = 1;
-    opt->vw_lower = 0;
-    opt->vw_upper = 0;
+    opt->long_row = 0;
     opt->spin_timeout_cycles = 0;
     opt->fault_row = -1;
+    opt->sf_ctas_per_sm = 0;
+    opt->sf_backoff_ns = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {
@@ -103,14 +104,16 @@ int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx, const jv_op
     jv_handle h = new jv_handle_s();
     if (opt) h->opt = *opt; else jv_default_options(&h->opt);
     if (h->opt.mode != JV_MODE_LEVEL && h->opt.mode != JV_MODE_SYNCFREE) { delete h; return JV_ERR_ARG; }
-    for (int v : {h->opt.vw_lower, h->opt.vw_upper})
-        if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8 && v != 16 && v != 32) { delete h; return JV_ERR_ARG; }
+    if (h->opt.long_row < 0 || h->opt.sf_ctas_per_sm < 0) { delete h; return JV_ERR_ARG; }
     h->n = n;
     h->nnz = nnz;
     h->stream = static_cast<cudaStream_t>(stream);
-    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return JV_ERR_CUDA; }
-    if (cudaMalloc(&h->flags, (size_t)n * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->ticket, 4 * sizeof(unsigned)) != cudaSuccess ||
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return JV_ERR_CUDA;
+    }
+    if (cudaMalloc(&h->ticket, 4 * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&h->status, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->h_status, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
@@ -225,8 +228,10 @@ int jv_get_info(jv_handle h, jv_info *info) {
     info->nnz_upper = h->nnz_upper;
     for (int k = 0; k < 4; ++k) {
         info->nlev[k] = h->ls[k].nlev;
-        info->vw[k] = h->ls[k].vw;
+        info->nlong[k] = h->ls[k].bins.nlong;
     }
+    info->nlong_factor = h->fbins.nlong;
+    info->npairs = h->npairs;
     info->mode = h->opt.mode;
     info->reorder = h->opt.reorder;
     return JV_OK;

@@ -1,191 +1,401 @@
 // Numeric ILU(0) on A's own pattern -- Sec. III, Fig. 1 (up-looking: row by
-// row, every row "looks up" at the already-factored rows it depends on).
+// row, every row "looks up" at the already-factored rows it depends on):
 //
-// A group of VW lanes owns one row r:
-//   for every col k < r of row r, in ascending order:
-//       wait until row k is final                     (sync-free mode only)
-//       a_rk <- a_rk / a_kk
-//       for every update column j > k of row k (split over the VW lanes):
-//           if j is in row r (binary search in r's sorted columns):
-//               a_rj <- a_rj - a_rk * a_kj
-// then the pivot a_rr is tested and the row is published.  Each entry of the
-// row receives its updates in ascending k and every product / difference /
-// quotient is rounded separately (__dmul_rn etc.), so the result is the same
-// IEEE sequence as the serial algorithm, bit for bit.
+//   for every col k < r of row r, in ascending order (entry p = (r, k)):
+//       l_rk = a_rk / u_kk
+//       for every precomputed pair (t, q) of p:      (t = (r, j), q = (k, j), j > k)
+//           a_rt = a_rt - l_rk * u_kq                (one fused multiply-add)
 //
-// LEVEL mode: one launch per level of lower(A) (rows of a level are
-// independent -- Sec. III: up-looking ILU has the dependency structure of a
-// triangular solve).  SYNCFREE mode: one launch; CTAs take tickets in level
-// order, and a row waits on a per-row flag of each dependency (the
-// point-to-point synchronisation of Sec. III-A, Fig. 4), released after the
-// row's values are stored and fenced.
+// Every entry receives its updates in ascending k, with the same IEEE
+// operations as the serial algorithm, so the factor equals it bit for bit.
+// The pairs come from the symbolic pass of the analysis (the update
+// structure of Fig. 1 depends only on the pattern).
+//
+// A row's U operands are u_kk for each lower entry, then u_kq for each pair,
+// in the order the steps consume them.  A task first loads, in one batch of
+// independent loads, everything the row needs that does not depend on other
+// rows: its values, the positions of its operands, its pair targets and step
+// boundaries -- into shared memory.  After that, waiting costs one memory
+// round trip per poll and the arithmetic touches shared memory only.
+//
+// Work list (see Bins): a short task holds up to 32 rows of one level, one
+// lane per row (a per-lane slot interleaved across the warp's shared memory);
+// every lane polls its next kPoll operands, keeps the ready prefix, and
+// factors and publishes its row as soon as the last one arrives -- no lane
+// waits for another's dependencies.  A long task is one row run by the whole
+// warp (operands prefetched, pairs split over the lanes, steps in order);
+// rows too large for the warp's shared memory work in a global scratch area
+// and await each operand when they use it.
+//
+// LEVEL mode: one launch per level of lower(A) (Sec. III-A: up-looking ILU has
+// the dependency structure of a triangular solve).  SYNCFREE mode (the
+// point-to-point synchronisation of Sec. III-A, Fig. 4): one persistent
+// launch; the output array is the synchronisation -- lu is first filled with
+// a sentinel bit pattern, a finished row publishes each U value with one
+// store, and a dependant polls only the U values it reads.
 #include "jv_internal.cuh"
 
 namespace jv {
 namespace {
 
+// Shared memory per warp.  Lane layout: kLaneSlot values (8 B), operand
+// positions (4 B) and pair targets / step ends (1 B each) per lane, each
+// interleaved across the 32 lanes.
+constexpr int kValBytes = kWarp * kLaneSlot * 8;
+constexpr int kWarpSmem = kValBytes + kWarp * kLaneSlot * (4 + 1 + 1);
+
 struct FactorArgs {
-    const int *rowptr, *colidx, *diag;
+    const int *rowptr, *diag, *kdiag, *pair_ptr;
+    const int2 *pairs;
     const int *rows, *task_lo, *task_hi;
     int task_begin, task_end;     // LEVEL: this level's tasks; SYNCFREE: all tasks
-    const void *vals;
-    void *lu;
-    int *flags;
-    unsigned *ticket;             // [0] next ticket, [1] finished CTAs
+    const void *vals;             // A's values (TV)
+    void *lu;                     // factor (TL); sentinel-filled in SYNCFREE mode
+    void *scratch;                // TL[nnz] work area for long rows that overflow the slot
+    unsigned *ticket;
     unsigned long long *status;
     long long timeout;
+    unsigned backoff_ns;
     int fault_row;
 };
 
 template <class T> struct RN;
 template <> struct RN<double> {
-    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
-    __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ static double fms(double a, double b, double c) { return __fma_rn(-a, b, c); }
     __device__ static double div(double a, double b) { return __ddiv_rn(a, b); }
 };
 template <> struct RN<float> {
-    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
-    __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ static float fms(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
     __device__ static float div(float a, float b) { return __fdiv_rn(a, b); }
 };
 
-__device__ __forceinline__ int find_col(const int *__restrict__ col, int lo, int hi, int j) {
-    int end = hi;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (__ldg(col + mid) < j) lo = mid + 1; else hi = mid;
+// Bounded spin until the U value at p is published; `u` is a first read.
+template <class T>
+__device__ __forceinline__ typename Bits<T>::U settle(const T *p, typename Bits<T>::U u,
+                                                      const FactorArgs &a, int r) {
+    using B = Bits<T>;
+    using U = typename B::U;
+    if (u != B::kSent) return u;
+    const long long t0 = clock64();
+    unsigned it = 0;
+    for (;;) {
+        sf_pause(it, a.backoff_ns);
+        u = ld_relaxed(reinterpret_cast<const U *>(p));
+        if (u != B::kSent) return u;
+        if ((++it & 15u) == 0) {
+            if (sf_aborted(a.ticket)) {           // another wait gave up: so does this row
+                report(a.status, JV_ERR_TIMEOUT, r);
+                return B::kCanonNan;
+            }
+            if (clock64() - t0 > a.timeout) {
+                report(a.status, JV_ERR_TIMEOUT, r);
+                sf_abort(a.ticket);
+                return B::kCanonNan;
+            }
+        }
     }
-    return (lo < end && __ldg(col + lo) == j) ? lo : -1;
 }
 
-// Bounded wait on a per-row flag: relaxed polling, then one fence (the
-// acquire half of the flag's release/acquire pair).  Gives up after the
-// cycle budget, or as soon as another wait of the launch has given up.
-__device__ __forceinline__ void wait_flag(const FactorArgs &a, int k, int r) {
-    if (ld_relaxed_s32(a.flags + k) == 0) {
-        const long long t0 = clock64();
-        unsigned it = 0;
-        while (ld_relaxed_s32(a.flags + k) == 0) {
-            if ((++it & 31u) == 0) {
-                if (sf_aborted(a.ticket)) break;
-                if (clock64() - t0 > a.timeout) {
+template <class T, bool SF>
+__device__ __forceinline__ typename Bits<T>::U first_read(const T *p) {
+    using U = typename Bits<T>::U;
+    if constexpr (SF) return ld_relaxed(reinterpret_cast<const U *>(p));
+    else return *reinterpret_cast<const U *>(p);
+}
+
+template <class T>
+__device__ __forceinline__ void publish(T *p, T v) {
+    using B = Bits<T>;
+    typename B::U u = isnan(v) ? B::kCanonNan : B::to(v);
+    st_relaxed(reinterpret_cast<typename B::U *>(p), u);
+}
+
+__device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, double d) {
+    if (d == 0.0 || !isfinite(d)) report(a.status, JV_ERR_ZERO_PIVOT, r);
+}
+
+// ------------------------------------------------------- one lane per row
+template <class TV, class TL, bool SF>
+__device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi,
+                                             unsigned char *smem) {
+    using B = Bits<TL>;
+    using U = typename B::U;
+    const int lane = threadIdx.x & 31;
+    TL *vb = reinterpret_cast<TL *>(smem) + lane;
+    int *ob = reinterpret_cast<int *>(smem + kValBytes) + lane;
+    unsigned char *tb = smem + kValBytes + kWarp * kLaneSlot * 4 + lane;
+    unsigned char *eb = tb + kWarp * kLaneSlot;
+    auto V = [&](int e) -> TL & { return vb[e * kWarp]; };           // values, then operands
+    auto OPOS = [&](int e) -> int & { return ob[e * kWarp]; };       // operand positions
+    auto TGT = [&](int i) -> unsigned char & { return tb[i * kWarp]; };
+    auto STEP_END = [&](int p) -> unsigned char & { return eb[p * kWarp]; };
+    const int pos = lo + lane;
+    bool done = pos >= hi;
+    int r = 0, rs = 0, len = 0, nl = 0, m = 0, got = 0;
+    TL *lu = static_cast<TL *>(a.lu);
+    if (!done) {
+        r = __ldg(a.rows + pos);
+        rs = __ldg(a.rowptr + r);
+        len = __ldg(a.rowptr + r + 1) - rs;
+        nl = __ldg(a.diag + r) - rs;
+        const int j0 = __ldg(a.pair_ptr + rs);
+        const int np = __ldg(a.pair_ptr + rs + nl) - j0;
+        m = nl + np;
+        const TV *vals = static_cast<const TV *>(a.vals);
+        TL v[kLaneSlot];
+        int kd[kLaneSlot], se[kLaneSlot];
+        int2 pr[kLaneSlot];
+#pragma unroll
+        for (int e = 0; e < kLaneSlot; ++e) {
+            if (e < len) v[e] = (TL)__ldg(vals + rs + e);
+            if (e < nl) kd[e] = __ldg(a.kdiag + rs + e);
+            if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
+            if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
+        }
+#pragma unroll
+        for (int e = 0; e < kLaneSlot; ++e) {
+            if (e < len) V(e) = v[e];
+            if (e < nl) { OPOS(e) = kd[e]; STEP_END(e) = (unsigned char)(se[e] - j0); }
+            if (e < np) { OPOS(nl + e) = pr[e].y; TGT(e) = (unsigned char)(pr[e].x - rs); }
+        }
+    }
+    long long t0 = 0;
+    unsigned rounds = 0;
+    int wb = 0, wend = 0;
+    U u[kPoll];
+    while (__any_sync(0xffffffffu, !done)) {
+        if (done) continue;
+        if (got == wend) {              // next window of operands [wb, wend)
+            wb = got;
+            wend = min(got + kPoll, m);
+        }
+        // (re-)read every operand of the window not taken yet; they tend to be
+        // published together, so they are all polled in the same round
+#pragma unroll
+        for (int k = 0; k < kPoll; ++k)
+            if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(lu + OPOS(wb + k));
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < kPoll; ++k) {
+            if (wb + k < got) continue;
+            if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
+                V(len + wb + k) = B::from(u[k]);
+                ++got;
+            } else {
+                ok = false;
+            }
+        }
+        if (got == m) {
+            int j = 0;
+            for (int p = 0; p < nl; ++p) {
+                const TL lik = RN<TL>::div(V(p), V(len + p));
+                for (const int j1 = STEP_END(p); j < j1; ++j) {
+                    const int t = TGT(j);
+                    V(t) = RN<TL>::fms(lik, V(len + nl + j), V(t));
+                }
+                V(p) = lik;
+            }
+            pivot_check(a, r, (double)V(nl));
+            for (int e = 0; e < len; ++e) {
+                if (!SF || e < nl) lu[rs + e] = V(e);
+                else if (r != a.fault_row) publish<TL>(lu + rs + e, V(e));
+            }
+            done = true;
+        } else if (SF && got < wend) {
+            if (rounds++ == 0) t0 = clock64();
+            if ((rounds & 15u) == 0) {
+                if (sf_aborted(a.ticket) || clock64() - t0 > a.timeout) {
                     report(a.status, JV_ERR_TIMEOUT, r);
                     sf_abort(a.ticket);
-                    break;
+                    done = true;
                 }
             }
         }
     }
-    __threadfence();
 }
 
-// Values of an already-published row written by another SM: in sync-free
-// mode read them at L2 (relaxed, gpu scope) rather than from a possibly
-// stale L1 line; in level mode a kernel boundary separates writer and reader.
-template <class T, bool SF>
-__device__ __forceinline__ T ld_row(const T *p) {
-    if constexpr (SF) {
-        using U = typename Bits<T>::U;
-        return Bits<T>::from(ld_relaxed(reinterpret_cast<const U *>(p)));
-    } else {
-        return *p;
-    }
-}
-
-__device__ __forceinline__ int take_task(const FactorArgs &a, bool syncfree) {
-    const int wib = threadIdx.x >> 5;
-    if (syncfree) return sf_take_ticket(a.ticket) * kWarpsPerBlock + wib;
-    return a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-}
-
-template <class TV, class TL, int VW, bool SF>
-__global__ void __launch_bounds__(kBlock) k_ilu0(FactorArgs a) {
-    const int task = take_task(a, SF);
-    if (task < a.task_end) {
-        const int lane = threadIdx.x & 31;
-        const int g = lane / VW, sub = lane % VW;
-        const unsigned gmask = (VW == 32) ? 0xffffffffu : (((1u << VW) - 1u) << (g * VW));
-        const int pos = a.task_lo[task] + g;
-        if (pos < a.task_hi[task]) {
-            const int r = a.rows[pos];
-            const int rs = a.rowptr[r], re = a.rowptr[r + 1], rd = a.diag[r];
-            TL *lu = static_cast<TL *>(a.lu);
-            const TV *vals = static_cast<const TV *>(a.vals);
-            if ((const void *)vals != (const void *)lu)
-                for (int p = rs + sub; p < re; p += VW) lu[p] = (TL)vals[p];
-            __syncwarp(gmask);
-            for (int p = rs; p < rd; ++p) {
-                const int k = __ldg(a.colidx + p);
-                if (SF) wait_flag(a, k, r);
-                const int kd = __ldg(a.diag + k), ke = __ldg(a.rowptr + k + 1);
-                const TL lik = RN<TL>::div(lu[p], ld_row<TL, SF>(lu + kd));
-                __syncwarp(gmask);
-                if (sub == 0) lu[p] = lik;
-                for (int q = kd + 1 + sub; q < ke; q += VW) {
-                    const int t = find_col(a.colidx, p + 1, re, __ldg(a.colidx + q));
-                    if (t >= 0) lu[t] = RN<TL>::sub(lu[t], RN<TL>::mul(lik, ld_row<TL, SF>(lu + q)));
+// ------------------------------------------------------- one warp per row
+template <class TV, class TL, bool SF>
+__device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsigned char *smem) {
+    using B = Bits<TL>;
+    using U = typename B::U;
+    const int lane = threadIdx.x & 31;
+    const int r = __ldg(a.rows + pos);
+    const int rs = __ldg(a.rowptr + r), re = __ldg(a.rowptr + r + 1), rd = __ldg(a.diag + r);
+    const int len = re - rs, nl = rd - rs;
+    const int j0 = __ldg(a.pair_ptr + rs);
+    const int np = __ldg(a.pair_ptr + rd) - j0;
+    const int m = nl + np;
+    TL *lu = static_cast<TL *>(a.lu);
+    const TV *vals = static_cast<const TV *>(a.vals);
+    const size_t need = (size_t)(len + m) * sizeof(TL) + (size_t)(np + nl) * sizeof(int);
+    const bool fast = need <= (size_t)kWarpSmem;
+    TL *w = fast ? reinterpret_cast<TL *>(smem) : static_cast<TL *>(a.scratch) + rs;
+    TL *uv = w + len;
+    int *tgt = reinterpret_cast<int *>(uv + m);                // fast path only
+    int *send = tgt + np;
+    for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
+    if (fast) {
+        for (int e = lane; e < np; e += kWarp) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
+        for (int e = lane; e < nl; e += kWarp) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
+        for (int e0 = 0; e0 < m; e0 += kWarp * kUnroll) {
+            int src[kUnroll];
+            U u[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int e = e0 + k * kWarp + lane;
+                src[k] = -1;
+                if (e < m) {
+                    src[k] = e < nl ? __ldg(a.kdiag + rs + e) : __ldg(a.pairs + j0 + e - nl).y;
+                    u[k] = first_read<TL, SF>(lu + src[k]);
                 }
-                __syncwarp(gmask);
             }
-            if (sub == 0) {
-                const double d = (double)lu[rd];
-                if (d == 0.0 || !isfinite(d)) report(a.status, JV_ERR_ZERO_PIVOT, r);
-            }
-            if (SF) {
-                __threadfence();
-                __syncwarp(gmask);
-                if (sub == 0 && r != a.fault_row) st_release(a.flags + r, 1);
-            }
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k)
+                if (src[k] >= 0) {
+                    if (SF) u[k] = settle<TL>(lu + src[k], u[k], a, r);
+                    uv[e0 + k * kWarp + lane] = B::from(u[k]);
+                }
         }
     }
-    if (SF) sf_finish(a.ticket);
+    __syncwarp();
+    int jb = 0;
+    for (int p = 0; p < nl; ++p) {
+        TL ukk;
+        if (fast) {
+            ukk = uv[p];
+        } else {
+            const TL *src = lu + __ldg(a.kdiag + rs + p);
+            ukk = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r) : first_read<TL, SF>(src));
+        }
+        const TL lik = RN<TL>::div(w[p], ukk);
+        const int je = fast ? send[p] : __ldg(a.pair_ptr + rs + p + 1) - j0;
+        for (int j = jb + lane; j < je; j += kWarp) {
+            int t;
+            TL uq;
+            if (fast) {
+                t = tgt[j];
+                uq = uv[nl + j];
+            } else {
+                const int2 tq = __ldg(a.pairs + j0 + j);
+                t = tq.x - rs;
+                const TL *src = lu + tq.y;
+                uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r) : first_read<TL, SF>(src));
+            }
+            w[t] = RN<TL>::fms(lik, uq, w[t]);
+        }
+        jb = je;
+        __syncwarp();
+        if (lane == 0) w[p] = lik;
+    }
+    __syncwarp();
+    if (lane == 0) pivot_check(a, r, (double)w[nl]);
+    for (int e = lane; e < len; e += kWarp) {
+        const TL v = w[e];
+        if (!SF || e < nl) lu[rs + e] = v;
+        else if (r != a.fault_row) publish<TL>(lu + rs + e, v);
+    }
+    __syncwarp();                                              // shared memory reusable
 }
 
 template <class TV, class TL, bool SF>
-int launch_vw(int vw, int grid, cudaStream_t s, const FactorArgs &a) {
-    count_launch();
-    switch (vw) {
-        case 1: k_ilu0<TV, TL, 1, SF><<<grid, kBlock, 0, s>>>(a); break;
-        case 2: k_ilu0<TV, TL, 2, SF><<<grid, kBlock, 0, s>>>(a); break;
-        case 4: k_ilu0<TV, TL, 4, SF><<<grid, kBlock, 0, s>>>(a); break;
-        case 8: k_ilu0<TV, TL, 8, SF><<<grid, kBlock, 0, s>>>(a); break;
-        case 16: k_ilu0<TV, TL, 16, SF><<<grid, kBlock, 0, s>>>(a); break;
-        default: k_ilu0<TV, TL, 32, SF><<<grid, kBlock, 0, s>>>(a); break;
+__device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
+    const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
+    if (hi & kLongBit) factor_warp<TV, TL, SF>(a, lo, smem);
+    else factor_lanes<TV, TL, SF>(a, lo, hi, smem);
+    __syncwarp();
+}
+
+template <class TV, class TL, bool SF>
+__global__ void __launch_bounds__(kBlock) k_ilu0(FactorArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int wib = threadIdx.x >> 5;
+    unsigned char *smem = dyn_smem + (size_t)wib * kWarpSmem;
+    if (SF) {
+        for (int base; (base = sf_next_chunk(a.ticket, a.task_end)) >= 0;)
+            if (base + wib < a.task_end) factor_task<TV, TL, SF>(a, base + wib, smem);
+        sf_finish(a.ticket);
+    } else {
+        const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
+        if (task < a.task_end) factor_task<TV, TL, SF>(a, task, smem);
     }
+}
+
+constexpr int kBlockSmem = kWarpsPerBlock * kWarpSmem;
+
+// Scratch: [0, nnz) work area for long rows, [nnz, 2 nnz) copy of the input
+// for in-place calls (8-byte elements, enough for either dtype).
+int ensure_scratch(jv_handle h) {
+    const size_t need = 2 * (size_t)h->nnz * sizeof(double) + 64;
+    if (h->fscratch_bytes >= need) return JV_OK;
+    if (h->fscratch) {
+        JV_CUDA(cudaStreamSynchronize(h->stream));
+        cudaFree(h->fscratch);
+        h->fscratch = nullptr;
+        h->fscratch_bytes = 0;
+    }
+    if (cudaMalloc(&h->fscratch, need) != cudaSuccess) {
+        cudaGetLastError();
+        h->fscratch = nullptr;
+        return JV_ERR_NOMEM;
+    }
+    h->fscratch_bytes = need;
+    return JV_OK;
+}
+
+template <class TV, class TL, bool SF>
+int launch(int grid, cudaStream_t s, const FactorArgs &a) {
+    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kBlockSmem));
+    count_launch();
+    k_ilu0<TV, TL, SF><<<grid, kBlock, kBlockSmem, s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }
 
 template <class TV, class TL>
 int run(jv_handle h, const void *vals, void *lu) {
+    const Bins &W = h->fbins;
     const LevelSet &L = h->ls[JV_LOWER];
     cudaStream_t s = h->stream;
+    const bool inplace = vals == lu;
+    if (inplace || W.nlong > 0) {
+        int rc = ensure_scratch(h);
+        if (rc) return rc;
+    }
+    if (inplace) {
+        void *copy = static_cast<char *>(h->fscratch) + (size_t)h->nnz * sizeof(double);
+        JV_CUDA(cudaMemcpyAsync(copy, vals, (size_t)h->nnz * sizeof(TV), cudaMemcpyDeviceToDevice, s));
+        vals = copy;
+    }
     FactorArgs a;
     a.rowptr = h->rowptr;
-    a.colidx = h->colidx;
     a.diag = h->diag;
-    a.rows = L.rows;
-    a.task_lo = L.task_lo;
-    a.task_hi = L.task_hi;
+    a.kdiag = h->kdiag;
+    a.pair_ptr = h->pair_ptr;
+    a.pairs = h->pairs;
+    a.rows = W.rows;
+    a.task_lo = W.task_lo;
+    a.task_hi = W.task_hi;
     a.vals = vals;
     a.lu = lu;
-    a.flags = h->flags;
+    a.scratch = h->fscratch;
     a.ticket = h->ticket;
     a.status = h->status;
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
+    a.backoff_ns = sf_backoff(h);
     if (h->opt.mode == JV_MODE_SYNCFREE) {
-        int rc = fill_u32(h->flags, (size_t)h->n, 0u, s);
+        int rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
         if (rc) return rc;
         a.task_begin = 0;
-        a.task_end = L.ntasks;
-        return launch_vw<TV, TL, true>(L.vw, grid_for(L.ntasks, kWarpsPerBlock), s, a);
+        a.task_end = W.ntasks;
+        return launch<TV, TL, true>(sf_grid(h, W.ntasks), s, a);
     }
     for (int l = 0; l < L.nlev; ++l) {
-        a.task_begin = L.h_task_ptr[l];
-        a.task_end = L.h_task_ptr[l + 1];
-        int rc = launch_vw<TV, TL, false>(L.vw, grid_for(a.task_end - a.task_begin, kWarpsPerBlock),
-                                          s, a);
+        a.task_begin = W.h_task_ptr[l];
+        a.task_end = W.h_task_ptr[l + 1];
+        int rc = launch<TV, TL, false>(grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
         if (rc) return rc;
     }
     return JV_OK;

@@ -16,6 +16,12 @@ constexpr int kWarp = 32;
 constexpr int kBlock = 256;              // threads per CTA for every kernel here
 constexpr int kWarpsPerBlock = kBlock / kWarp;
 constexpr long long kDefaultSpin = 1ll << 32;
+constexpr int kUnroll = 4;        // entries per lane per step (cooperative kernels)
+constexpr int kPoll = 8;          // operands polled per lane per round (one-lane-per-row kernels)
+constexpr int kLongDeps = 24;     // solve rows with more dependencies run one per warp
+constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
+constexpr int kSpmvRows = 256;    // rows per spmv block (one summing thread each)
+constexpr int kSpmvCap = 2048;    // nonzeros per spmv block (8 per thread)
 
 // ---------------------------------------------------------------- launches
 extern std::atomic<unsigned long long> g_launches;
@@ -47,16 +53,17 @@ inline int grid_for(long long work, int per_block) {
 }
 
 // ------------------------------------------------------------- device status
-// One 64-bit word per handle: min over reported errors of (row << 32 | -code),
-// so the smallest failing row wins and the word reads ~0 when all is well.
+// One 64-bit word per handle: min over reported errors of (row << 32 | 16 + code),
+// so the smallest failing row wins, and on one row a timeout (the cause)
+// outranks the non-finite pivot it produces.  The word reads ~0 when all is well.
 __device__ __forceinline__ void report(unsigned long long *st, int code, int row) {
-    unsigned long long key = ((unsigned long long)(unsigned)row << 32) | (unsigned)(-code);
+    unsigned long long key = ((unsigned long long)(unsigned)row << 32) | (unsigned)(16 + code);
     atomicMin(st, key);
 }
 inline int decode_status(unsigned long long key, int *row) {
     if (key == ~0ull) { if (row) *row = -1; return JV_OK; }
     if (row) *row = (int)(key >> 32);
-    return -(int)(key & 0xffffffffu);
+    return (int)(key & 0xffffffffu) - 16;
 }
 
 // ------------------------------------------------------ memory-order helpers
@@ -91,18 +98,32 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
 }
 
 // ------------------------------------------------------ sync-free launches
-// Three words per handle: [0] next CTA ticket, [1] finished CTAs, [2] abort.
-// CTAs take tickets in launch order, so every task a CTA waits on belongs to
-// a CTA that is already running (or done): no wait can depend on a CTA that
-// is not resident.  The last CTA to finish resets all three words, so the
-// next launch starts from zero without a memset.  A wait that exceeds its
-// cycle budget reports JV_ERR_TIMEOUT and raises the abort word; every other
-// wait polls it and gives up too, so a fault costs one timeout period.
-__device__ __forceinline__ int sf_take_ticket(unsigned *ticket) {
-    __shared__ unsigned s_ticket;
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+// Three words per handle: [0] next chunk ticket, [1] finished CTAs, [2] abort.
+// A sync-free launch is a fixed grid of persistent CTAs; each CTA repeatedly
+// claims the next chunk of kWarpsPerBlock level-ordered tasks with one atomic
+// and runs it.  A chunk is only ever claimed by a running CTA and every task
+// waits only on tasks of earlier chunks, so no wait depends on a CTA that is
+// not resident, and the grid size bounds how far ahead of the dependency
+// front the GPU runs (how many rows poll at once).  The last CTA to finish
+// resets all three words, so the next launch starts from zero without a
+// memset.  A wait that exceeds its cycle budget reports JV_ERR_TIMEOUT and
+// raises the abort word; every other wait polls it and gives up too, so a
+// fault costs one timeout period.
+//
+// Returns the first task of the CTA's next chunk, or -1 (block-uniform).
+__device__ __forceinline__ int sf_next_chunk(unsigned *ticket, int ntasks) {
+    __shared__ int s_base;
     __syncthreads();
-    return (int)s_ticket;
+    if (threadIdx.x == 0) s_base = (int)atomicAdd(ticket, 1u) * kWarpsPerBlock;
+    __syncthreads();
+    return s_base < ntasks ? s_base : -1;
+}
+
+// Back-off between polls of a word that is not ready yet.
+__device__ __forceinline__ void sf_pause(unsigned it, unsigned max_ns) {
+    if (max_ns == 0 || it < 4) return;
+    unsigned ns = 16u << min(it - 4u, 6u);
+    __nanosleep(ns < max_ns ? ns : max_ns);
 }
 __device__ __forceinline__ void sf_finish(unsigned *ticket) {
     __syncthreads();
@@ -152,19 +173,40 @@ struct Span {
     __device__ __forceinline__ int at(int i) const { return __ldg(a + i + ai) + ad; }
 };
 
+// Position of column j in the sorted column range [lo, hi), or -1.
+__device__ __forceinline__ int find_col(const int *__restrict__ col, int lo, int hi, int j) {
+    const int end = hi;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(col + mid) < j) lo = mid + 1; else hi = mid;
+    }
+    return (lo < end && __ldg(col + lo) == j) ? lo : -1;
+}
+
 // -------------------------------------------------------------- level sets
+// Work list of one level structure, rows binned by cost (the row-length
+// classes of the load-balancing concern of Sec. III-A / III-B): inside every
+// level the short rows come first, in ascending order, packed 32 to a task
+// with one lane per row; every long row is a task of its own, run by the
+// whole warp.  A task never spans two levels, so the rows of a task never
+// depend on each other.
+constexpr int kLongBit = (int)0x80000000u;   // task_hi flag: one-row cooperative task
+struct Bins {
+    int *rows = nullptr;       // [n] binned rows
+    int *task_lo = nullptr;    // [ntasks] first position in rows
+    int *task_hi = nullptr;    // [ntasks] end position, | kLongBit for a long-row task
+    int ntasks = 0;
+    int nlong = 0;
+    std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
+};
+
 struct LevelSet {
     int nlev = 0;
     int *lev = nullptr;        // [n] level of every row
     int *ptr = nullptr;        // [nlev+1]
     int *rows = nullptr;       // [n] rows grouped by level, ascending inside
     std::vector<int> h_ptr;    // host copy of ptr
-    int vw = 1;                // lanes per row for the single-RHS kernels
-    int rows_per_task = 32;    // 32 / vw
-    int ntasks = 0;
-    int *task_lo = nullptr;    // [ntasks] positions in rows[]; a task never spans two levels
-    int *task_hi = nullptr;
-    std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
+    Bins bins;                 // single right-hand-side solve work list
 };
 
 struct Workspace;  // Krylov scratch, krylov.cu
@@ -184,18 +226,43 @@ struct jv_handle_s {
     jv::LevelSet ls[4];
     // reordering
     int *perm = nullptr, *iperm = nullptr, *vmap = nullptr;
+    // symbolic factorisation: for every strictly lower entry p = (r, k) the
+    // updates it drives, pairs (t, q) with a_rt -= l_rk * u_kq, t ascending
+    int *pair_ptr = nullptr;                 // [nnz + 1], empty ranges off the strict lower part
+    int2 *pairs = nullptr;                   // [npairs] (t, q) absolute CSR positions
+    int *kdiag = nullptr;                    // [nnz] diag[colidx[p]]: position of u_kk for p = (r, k)
+    long long npairs = 0;
+    jv::Bins fbins;                          // factor work list over the levels of lower(A)
+    int maxrow = 0;                          // longest row
+    // spmv row blocks: block b covers rows [spmv_blk[b], spmv_blk[b+1])
+    int *spmv_blk = nullptr;
+    int nspmv_blk = 0;
+    // lazily allocated factor scratch (long rows / in-place copies)
+    void *fscratch = nullptr;
+    size_t fscratch_bytes = 0;
     // scratch shared by the sync-free kernels
-    int *flags = nullptr;                    // [n] per-row "factored" flags
-    unsigned *ticket = nullptr;              // [2]: next CTA ticket, finished CTAs
+    unsigned *ticket = nullptr;              // [4]: next CTA ticket, finished CTAs, abort
     unsigned long long *status = nullptr;    // device status word
     unsigned long long *h_status = nullptr;  // pinned host mirror
-    int spmv_vw = 8;
     int bad_row = -1;                        // row of the last analysis error
+    int num_sms = 152;
     jv::Workspace *ws = nullptr;
     std::vector<void *> allocs;              // everything to cudaFree on destroy
 };
 
 namespace jv {
+
+// Persistent grid of a sync-free launch over `ntasks` tasks, and the poll
+// back-off bound, from the handle's options.
+inline int sf_grid(jv_handle h, int ntasks) {
+    const int per_sm = h->opt.sf_ctas_per_sm > 0 ? h->opt.sf_ctas_per_sm : 1;
+    const int chunks = (ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int g = h->num_sms * per_sm;
+    return chunks < g ? (chunks > 0 ? chunks : 1) : g;
+}
+inline unsigned sf_backoff(jv_handle h) {
+    return h->opt.sf_backoff_ns <= 0 ? 0u : (unsigned)h->opt.sf_backoff_ns;
+}
 
 // allocation owned by the handle
 int halloc(jv_handle h, void **p, size_t bytes);

@@ -7,57 +7,78 @@
 namespace jv {
 namespace {
 
-// A group of VW lanes per row; consecutive groups take consecutive rows, so a
-// warp reads one contiguous stretch of colidx / vals.
-template <class T, int VW>
-__global__ void __launch_bounds__(kBlock) k_spmv(int n, const int *__restrict__ rowptr,
+template <class T> struct RN;
+template <> struct RN<double> {
+    __device__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+};
+template <> struct RN<float> {
+    __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+};
+
+// One CTA per row block (at most kSpmvRows rows and kSpmvCap nonzeros, fixed
+// by the analysis): the block's nonzeros are streamed with fully coalesced
+// loads, each thread keeping several independent loads in flight, and staged
+// in shared memory together with the gathered x_j; then one thread per row
+// accumulates s = fma(a_ij, x_j, s) in ascending column order -- the serial
+// spmv's sequence, so the result is identical to it.  A row longer than the
+// cap has a block of its own and is walked in chunks.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_spmv(const int *__restrict__ blk,
+                                                 const int *__restrict__ rowptr,
                                                  const int *__restrict__ colidx,
                                                  const T *__restrict__ vals,
-                                                 const T *__restrict__ x, T *y, T alpha, T beta) {
-    constexpr int R = kWarp / VW;
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)kBlock + threadIdx.x) >> 5;
-    const long long r = warp * R + lane / VW;
-    const int sub = lane % VW;
-    T acc = 0;
-    if (r < n) {
-        const int e = __ldg(rowptr + r + 1);
-        for (int q = __ldg(rowptr + r) + sub; q < e; q += VW)
-            acc = fma(__ldg(vals + q), __ldg(x + __ldg(colidx + q)), acc);
-    }
-#pragma unroll
-    for (int o = VW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (r < n && sub == 0) {
-        T v = alpha * acc;
-        if (beta != (T)0) v = fma(beta, y[r], v);
-        y[r] = v;
+                                                 const T *__restrict__ x, T *y, T alpha, T beta,
+                                                 int has_beta) {
+    __shared__ T sv[kSpmvCap];
+    __shared__ T sx[kSpmvCap];
+    const int r0 = __ldg(blk + blockIdx.x), r1 = __ldg(blk + blockIdx.x + 1);
+    const int p0 = __ldg(rowptr + r0), p1 = __ldg(rowptr + r1);
+    const int tid = threadIdx.x;
+    if (p1 - p0 <= kSpmvCap) {
+        const int m = p1 - p0;
+#pragma unroll 8
+        for (int e = tid; e < m; e += kBlock) {
+            const int q = p0 + e;
+            sv[e] = __ldg(vals + q);
+            sx[e] = __ldg(x + __ldg(colidx + q));
+        }
+        __syncthreads();
+        for (int i = tid; i < r1 - r0; i += kBlock) {
+            const int r = r0 + i;
+            const int e1 = __ldg(rowptr + r + 1) - p0;
+            T s = 0;
+            for (int e = __ldg(rowptr + r) - p0; e < e1; ++e) s = RN<T>::fma(sv[e], sx[e], s);
+            T v = RN<T>::mul(alpha, s);
+            if (has_beta) v = RN<T>::fma(beta, y[r], v);
+            y[r] = v;
+        }
+    } else {
+        T s = 0;
+        for (int c0 = p0; c0 < p1; c0 += kSpmvCap) {
+            const int m = min(kSpmvCap, p1 - c0);
+#pragma unroll 8
+            for (int e = tid; e < m; e += kBlock) {
+                const int q = c0 + e;
+                sv[e] = __ldg(vals + q);
+                sx[e] = __ldg(x + __ldg(colidx + q));
+            }
+            __syncthreads();
+            if (tid == 0)
+                for (int e = 0; e < m; ++e) s = RN<T>::fma(sv[e], sx[e], s);
+            __syncthreads();
+        }
+        if (tid == 0) {
+            T v = RN<T>::mul(alpha, s);
+            if (has_beta) v = RN<T>::fma(beta, y[r0], v);
+            y[r0] = v;
+        }
     }
 }
 
-template <class T>
-int spmv_t(jv_handle h, const void *vals, const void *x, void *y, double alpha, double beta) {
-    const int vw = h->spmv_vw;
-    const long long rows_per_block = (long long)kWarpsPerBlock * (kWarp / vw);
-    const int grid = grid_for(h->n, (int)rows_per_block);
-    cudaStream_t s = h->stream;
-    const T *v = static_cast<const T *>(vals);
-    const T *xx = static_cast<const T *>(x);
-    T *yy = static_cast<T *>(y);
-    count_launch();
-    switch (vw) {
-        case 1: k_spmv<T, 1><<<grid, kBlock, 0, s>>>(h->n, h->rowptr, h->colidx, v, xx, yy, (T)alpha, (T)beta); break;
-        case 2: k_spmv<T, 2><<<grid, kBlock, 0, s>>>(h->n, h->rowptr, h->colidx, v, xx, yy, (T)alpha, (T)beta); break;
-        case 4: k_spmv<T, 4><<<grid, kBlock, 0, s>>>(h->n, h->rowptr, h->colidx, v, xx, yy, (T)alpha, (T)beta); break;
-        case 8: k_spmv<T, 8><<<grid, kBlock, 0, s>>>(h->n, h->rowptr, h->colidx, v, xx, yy, (T)alpha, (T)beta); break;
-        case 16: k_spmv<T, 16><<<grid, kBlock, 0, s>>>(h->n, h->rowptr, h->colidx, v, xx, yy, (T)alpha, (T)beta); break;
-        default: k_spmv<T, 32><<<grid, kBlock, 0, s>>>(h->n, h->rowptr, h->colidx, v, xx, yy, (T)alpha, (T)beta); break;
-    }
-    JV_CHECK_LAUNCH();
-    return JV_OK;
-}
-
-// g[p] = alpha * sum_c a[i,c] b[j,c] for the entries p = (i, j) of one part of
-// row i; one warp per row, lanes over the right-hand sides.
+// g[p] = alpha * sum_c a[i,c] b[j,c] over the entries p = (i, j) of one part of
+// row i: one warp per row, one lane per entry, the sum over c in order.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_masked_outer(int n, const int *rowptr, const int *colidx,
                                                          const int *diag, int which, const T *A,
@@ -68,13 +89,12 @@ __global__ void __launch_bounds__(kBlock) k_masked_outer(int n, const int *rowpt
     const int lo = which == 0 ? rowptr[i] : diag[i];
     const int hi = which == 0 ? diag[i] : rowptr[i + 1];
     const size_t ld = (size_t)nrhs;
-    for (int p = lo; p < hi; ++p) {
-        const int j = colidx[p];
+    const T *ai = A + i * ld;
+    for (int p = lo + lane; p < hi; p += 32) {
+        const T *bj = B + (size_t)__ldg(colidx + p) * ld;
         T s = 0;
-        for (int c = lane; c < nrhs; c += 32) s = fma(A[i * ld + c], B[(size_t)j * ld + c], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) g[p] = alpha * s;
+        for (int c = 0; c < nrhs; ++c) s = RN<T>::fma(__ldg(ai + c), __ldg(bj + c), s);
+        g[p] = RN<T>::mul(alpha, s);
     }
 }
 
@@ -97,9 +117,21 @@ __global__ void k_permute_rows(int n, int nrhs, const int *perm, int inverse, co
 
 int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, double alpha,
          double beta) {
-    if (t == JV_F64) return spmv_t<double>(h, vals, x, y, alpha, beta);
-    if (t == JV_F32) return spmv_t<float>(h, vals, x, y, alpha, beta);
-    return JV_ERR_ARG;
+    const int grid = h->nspmv_blk;
+    const int hb = beta != 0.0;
+    count_launch();
+    if (t == JV_F64)
+        k_spmv<double><<<grid, kBlock, 0, h->stream>>>(h->spmv_blk, h->rowptr, h->colidx,
+                                                       (const double *)vals, (const double *)x,
+                                                       (double *)y, alpha, beta, hb);
+    else if (t == JV_F32)
+        k_spmv<float><<<grid, kBlock, 0, h->stream>>>(h->spmv_blk, h->rowptr, h->colidx,
+                                                      (const float *)vals, (const float *)x,
+                                                      (float *)y, (float)alpha, (float)beta, hb);
+    else
+        return JV_ERR_ARG;
+    JV_CHECK_LAUNCH();
+    return JV_OK;
 }
 
 int masked_outer(jv_handle h, jv_dtype t, int which, const void *a, const void *b, int nrhs,

@@ -1,21 +1,30 @@
 // Sparse triangular solves ("stri", Sec. VI): forward substitution with the
 // unit lower factor, backward substitution with U, and the two transposed
-// solves of the adjoint, all reusing the level structure built by the
-// analysis (Sec. III-A: the factor and the solves share one DAG).
+// solves of the adjoint, all on the level structure built by the analysis
+// (Sec. III-A: the factor and the solves share one DAG).
 //
-// One row r computes x_r = (b_r - sum_j t_rj x_j) [/ u_rr], where the
-// dependency entries t_rj are a sub-range of row r of the CSR (L, U) or of
-// column r of the CSC (U^T, L^T; the value is fetched through csc2csr).
+// Row r computes s = b_r; s = s - t_rj x_j over its dependency entries in a
+// fixed order; x_r = s [/ u_rr].  The entries are a sub-range of row r of the
+// CSR (L, U) or of column r of the CSC (U^T, L^T, values fetched through
+// csc2csr).  The order is the one the serial substitution uses (ascending
+// columns; descending rows for L^T) and every update is one fused
+// multiply-add, so the result equals the serial solve bit for bit; only the
+// loads run in parallel.
 //
-// Single right-hand side: a group of VW lanes per row, partial sums reduced
-// by a fixed shuffle tree.  Several right-hand sides: one warp per row and
-// one lane per right-hand side (row-major n x nrhs, so the lanes read one
-// contiguous segment of every dependency row).
+// Work list (see Bins): a short task holds up to 32 rows of one level, one
+// lane per row.  Every lane polls the next kPoll dependencies of its own row,
+// consumes the ready prefix in order and publishes its row the moment the
+// last one arrives, so no lane waits for another lane's dependencies.  A
+// long task is one row with many dependencies; the whole warp loads 32 x
+// kUnroll of them at a time and replays the ordered chain through shuffles.
+// Several right-hand sides: one warp per row, one lane per right-hand side
+// (row-major n x nrhs: the lanes read one contiguous segment of every
+// dependency row).
 //
-// LEVEL mode: one launch per level.  SYNCFREE mode: one launch; CTAs take
-// tickets in level order and every dependency is awaited on its own output
-// word -- the output vector is pre-filled with a sentinel bit pattern and a
-// single relaxed store publishes a finished value (no fence, no flag).
+// LEVEL mode: one launch per level.  SYNCFREE mode: one persistent launch
+// over all levels (see sf_next_chunk); the output vector is pre-filled with a
+// sentinel bit pattern and one relaxed store publishes a finished value, so
+// each dependency is awaited on its own output word (no flags, no fences).
 #include "jv_internal.cuh"
 
 namespace jv {
@@ -27,6 +36,7 @@ struct TriArgs {
     const int *vmap;       // CSC -> CSR value position, or nullptr
     const int *diag;
     int unit;              // 1: unit diagonal (L, L^T)
+    int reverse;           // 1: walk the range from its end (L^T)
     const int *rows, *task_lo, *task_hi;
     int task_begin, task_end;
     const void *lu, *b;
@@ -35,44 +45,45 @@ struct TriArgs {
     unsigned *ticket;
     unsigned long long *status;
     long long timeout;
+    unsigned backoff_ns;
     int fault_row;
 };
 
-__device__ __forceinline__ int take_task(const TriArgs &a, bool syncfree) {
-    const int wib = threadIdx.x >> 5;
-    if (syncfree) return sf_take_ticket(a.ticket) * kWarpsPerBlock + wib;
-    return a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-}
+template <class T> struct RN;
+template <> struct RN<double> {
+    __device__ static double fms(double a, double b, double c) { return __fma_rn(-a, b, c); }
+    __device__ static double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+template <> struct RN<float> {
+    __device__ static float fms(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
+    __device__ static float div(float a, float b) { return __fdiv_rn(a, b); }
+};
 
-// Bounded wait until the dependency's output word no longer holds the
-// sentinel; gives up after the cycle budget or when another wait of the
-// launch has given up (the value is then a quiet NaN).
+// Spin (bounded) until *p no longer holds the sentinel; `u` is a first read.
 template <class TX>
-__device__ __forceinline__ TX wait_x(const TX *p, const TriArgs &a, int r) {
+__device__ __forceinline__ typename Bits<TX>::U settle(const TX *p, typename Bits<TX>::U u,
+                                                       const TriArgs &a, int r) {
     using B = Bits<TX>;
     using U = typename B::U;
-    U u = ld_relaxed(reinterpret_cast<const U *>(p));
-    if (u == B::kSent) {
-        const long long t0 = clock64();
-        unsigned it = 0;
-        for (;;) {
-            u = ld_relaxed(reinterpret_cast<const U *>(p));
-            if (u != B::kSent) break;
-            if ((++it & 31u) == 0) {
-                if (sf_aborted(a.ticket)) {
-                    u = B::kCanonNan;
-                    break;
-                }
-                if (clock64() - t0 > a.timeout) {
-                    report(a.status, JV_ERR_TIMEOUT, r);
-                    sf_abort(a.ticket);
-                    u = B::kCanonNan;
-                    break;
-                }
+    if (u != B::kSent) return u;
+    const long long t0 = clock64();
+    unsigned it = 0;
+    for (;;) {
+        sf_pause(it, a.backoff_ns);
+        u = ld_relaxed(reinterpret_cast<const U *>(p));
+        if (u != B::kSent) return u;
+        if ((++it & 15u) == 0) {
+            if (sf_aborted(a.ticket)) {           // another wait gave up: so does this row
+                report(a.status, JV_ERR_TIMEOUT, r);
+                return B::kCanonNan;
+            }
+            if (clock64() - t0 > a.timeout) {
+                report(a.status, JV_ERR_TIMEOUT, r);
+                sf_abort(a.ticket);
+                return B::kCanonNan;
             }
         }
     }
-    return B::from(u);
 }
 
 template <class TX>
@@ -82,102 +93,233 @@ __device__ __forceinline__ void publish(TX *p, TX v) {
     st_relaxed(reinterpret_cast<typename B::U *>(p), u);
 }
 
+template <class TX, bool SF>
+__device__ __forceinline__ typename Bits<TX>::U first_read(const TX *p) {
+    using U = typename Bits<TX>::U;
+    if constexpr (SF) return ld_relaxed(reinterpret_cast<const U *>(p));
+    else return *reinterpret_cast<const U *>(p);
+}
+
 template <class TL>
 __device__ __forceinline__ TL load_val(const TriArgs &a, int q) {
     const TL *lu = static_cast<const TL *>(a.lu);
     return a.vmap ? __ldg(lu + __ldg(a.vmap + q)) : __ldg(lu + q);
 }
 
-template <class TL, class TB, class TX, int VW, bool SF>
-__global__ void __launch_bounds__(kBlock) k_trsv(TriArgs a) {
-    const int task = take_task(a, SF);
-    if (task < a.task_end) {
-        const int lane = threadIdx.x & 31;
-        const int g = lane / VW, sub = lane % VW;
-        const int pos = a.task_lo[task] + g;
-        const bool act = pos < a.task_hi[task];
-        TX *x = static_cast<TX *>(a.x);
-        TL acc = 0;
-        int r = 0;
-        if (act) {
-            r = a.rows[pos];
-            const int e = a.end.at(r);
-            for (int q = a.beg.at(r) + sub; q < e; q += VW) {
-                const int j = __ldg(a.idx + q);
-                const TL v = load_val<TL>(a, q);
-                const TL xj = SF ? (TL)wait_x<TX>(x + j, a, r) : (TL)x[j];
-                acc = fma(v, xj, acc);
+template <class TL, class TX>
+__device__ __forceinline__ void store_x(const TriArgs &a, bool sf, TX *p, int r, TL v) {
+    if (sf) {
+        if (r != a.fault_row) publish<TX>(p, (TX)v);
+    } else {
+        *p = (TX)v;
+    }
+}
+
+// Short task: rows[lo..hi) of one level, one lane per row, polled independently.
+// The indices and values of the next kPoll dependencies (a window) are loaded
+// once; every poll round then re-reads only the x words still missing.
+template <class TL, class TB, class TX, bool SF>
+__device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
+    using B = Bits<TX>;
+    using U = typename B::U;
+    const int lane = threadIdx.x & 31;
+    const int pos = lo + lane;
+    TX *x = static_cast<TX *>(a.x);
+    bool done = pos >= hi;
+    int r = 0, qb = 0, len = 0, e = 0, wb = 0, wend = 0;
+    TL s = 0, d = 1;
+    int jw[kPoll];
+    TL vw[kPoll];
+    if (!done) {
+        r = __ldg(a.rows + pos);
+        qb = a.beg.at(r);
+        len = a.end.at(r) - qb;
+        s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
+        if (!a.unit) d = __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    }
+    U u[kPoll];
+    long long t0 = 0;
+    unsigned rounds = 0;
+    while (__any_sync(0xffffffffu, !done)) {
+        if (done) continue;
+        if (e == wend) {
+            // next window [wb, wend): indices, values and a first read of every x
+            wb = e;
+            wend = min(e + kPoll, len);
+#pragma unroll
+            for (int k = 0; k < kPoll; ++k)
+                if (wb + k < wend) {
+                    const int q = a.reverse ? qb + len - 1 - (wb + k) : qb + wb + k;
+                    jw[k] = __ldg(a.idx + q);
+                    vw[k] = load_val<TL>(a, q);
+                }
+        }
+        // (re-)read every entry of the window not consumed yet; dependencies
+        // tend to arrive together, so they are all polled in the same round
+#pragma unroll
+        for (int k = 0; k < kPoll; ++k)
+            if (wb + k >= e && wb + k < wend) u[k] = first_read<TX, SF>(x + jw[k]);
+        // consume the ready prefix, in order
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < kPoll; ++k) {
+            if (wb + k < e) continue;
+            if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
+                s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                ++e;
+            } else {
+                ok = false;
             }
         }
-#pragma unroll
-        for (int o = VW / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (act && sub == 0) {
-            TL xr = (TL)static_cast<const TB *>(a.b)[r] - acc;
-            if (!a.unit) xr = xr / static_cast<const TL *>(a.lu)[a.diag[r]];
-            if (SF) {
-                if (r != a.fault_row) publish<TX>(x + r, (TX)xr);
-            } else {
-                x[r] = (TX)xr;
+        if (e == len) {
+            store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+            done = true;
+        } else if (SF && e < wend) {
+            if (rounds++ == 0) t0 = clock64();
+            if ((rounds & 15u) == 0) {
+                if (sf_aborted(a.ticket) || clock64() - t0 > a.timeout) {
+                    report(a.status, JV_ERR_TIMEOUT, r);
+                    sf_abort(a.ticket);
+                    done = true;
+                }
             }
         }
     }
-    if (SF) sf_finish(a.ticket);
+}
+
+// Long task: one row, the whole warp loads its dependencies.
+template <class TL, class TB, class TX, bool SF>
+__device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
+    using B = Bits<TX>;
+    using U = typename B::U;
+    constexpr int CH = kWarp * kUnroll;
+    const int lane = threadIdx.x & 31;
+    TX *x = static_cast<TX *>(a.x);
+    const int r = __ldg(a.rows + pos);
+    const int qb = a.beg.at(r);
+    const int len = a.end.at(r) - qb;
+    TL s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
+    const TL d = a.unit ? (TL)1 : __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    for (int c0 = 0; c0 < len; c0 += CH) {
+        int q[kUnroll];
+        TL v[kUnroll];
+        U u[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            const int e = c0 + k * kWarp + lane;
+            q[k] = -1;
+            if (e < len) {
+                q[k] = a.reverse ? qb + len - 1 - e : qb + e;
+                v[k] = load_val<TL>(a, q[k]);
+                u[k] = first_read<TX, SF>(x + __ldg(a.idx + q[k]));
+            }
+        }
+        TL xv[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            xv[k] = 0;
+            if (q[k] >= 0) {
+                if (SF) u[k] = settle<TX>(x + __ldg(a.idx + q[k]), u[k], a, r);
+                xv[k] = (TL)B::from(u[k]);
+            } else {
+                v[k] = 0;
+            }
+        }
+        // the ordered chain: entry c0 + k*32 + l is held by lane l
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k)
+            for (int l = 0; l < kWarp; ++l) {
+                const TL vl = __shfl_sync(0xffffffffu, v[k], l);
+                const TL xl = __shfl_sync(0xffffffffu, xv[k], l);
+                if (c0 + k * kWarp + l < len) s = RN<TL>::fms(vl, xl, s);
+            }
+    }
+    if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+}
+
+template <class TL, class TB, class TX, bool SF>
+__device__ __forceinline__ void trsv_task(const TriArgs &a, int task) {
+    const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
+    if (hi & kLongBit) trsv_warp<TL, TB, TX, SF>(a, lo);
+    else trsv_lanes<TL, TB, TX, SF>(a, lo, hi);
+}
+
+template <class TL, class TB, class TX, bool SF>
+__global__ void __launch_bounds__(kBlock) k_trsv(TriArgs a) {
+    const int wib = threadIdx.x >> 5;
+    if (SF) {
+        for (int base; (base = sf_next_chunk(a.ticket, a.task_end)) >= 0;)
+            if (base + wib < a.task_end) trsv_task<TL, TB, TX, SF>(a, base + wib);
+        sf_finish(a.ticket);
+    } else {
+        const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
+        if (task < a.task_end) trsv_task<TL, TB, TX, SF>(a, task);
+    }
+}
+
+// Several right-hand sides: one warp per row (rows[task]), one lane per column.
+template <class TL, class TB, class TX, bool SF>
+__device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
+    using B = Bits<TX>;
+    using U = typename B::U;
+    const int lane = threadIdx.x & 31;
+    const int r = __ldg(a.rows + task);
+    const int qb = a.beg.at(r), len = a.end.at(r) - qb;
+    const size_t ld = (size_t)a.nrhs;
+    TX *x = static_cast<TX *>(a.x);
+    const TB *b = static_cast<const TB *>(a.b);
+    const TL d = a.unit ? (TL)1 : __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    for (int c0 = 0; c0 < a.nrhs; c0 += 32) {
+        const int c = c0 + lane;
+        const bool ok = c < a.nrhs;
+        TL s = ok ? (TL)b[(size_t)r * ld + c] : (TL)0;
+        for (int e0 = 0; e0 < len; e0 += kUnroll) {
+            int j[kUnroll];
+            TL v[kUnroll];
+            U u[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int e = e0 + k;
+                j[k] = -1;
+                if (e < len) {
+                    const int q = a.reverse ? qb + len - 1 - e : qb + e;
+                    j[k] = __ldg(a.idx + q);
+                    v[k] = load_val<TL>(a, q);
+                    if (ok) u[k] = first_read<TX, SF>(x + (size_t)j[k] * ld + c);
+                }
+            }
+            if (ok) {
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    if (j[k] >= 0) {
+                        if (SF) u[k] = settle<TX>(x + (size_t)j[k] * ld + c, u[k], a, r);
+                        s = RN<TL>::fms(v[k], (TL)B::from(u[k]), s);
+                    }
+                }
+            }
+        }
+        if (ok) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, a.unit ? s : RN<TL>::div(s, d));
+    }
 }
 
 template <class TL, class TB, class TX, bool SF>
 __global__ void __launch_bounds__(kBlock) k_trsm(TriArgs a) {
-    const int task = take_task(a, SF);
-    if (task < a.task_end) {
-        const int lane = threadIdx.x & 31;
-        const int r = a.rows[task];
-        const int s = a.beg.at(r), e = a.end.at(r);
-        const size_t ld = (size_t)a.nrhs;
-        TX *x = static_cast<TX *>(a.x);
-        const TB *b = static_cast<const TB *>(a.b);
-        const bool unit = a.unit;
-        const TL d = unit ? (TL)1 : static_cast<const TL *>(a.lu)[a.diag[r]];
-        for (int c0 = 0; c0 < a.nrhs; c0 += 32) {
-            const int c = c0 + lane;
-            const bool ok = c < a.nrhs;
-            TL acc = 0;
-            for (int q = s; q < e; ++q) {
-                const int j = __ldg(a.idx + q);
-                const TL v = load_val<TL>(a, q);
-                if (ok) {
-                    const TX *xp = x + (size_t)j * ld + c;
-                    const TL xj = SF ? (TL)wait_x<TX>(xp, a, r) : (TL)*xp;
-                    acc = fma(v, xj, acc);
-                }
-            }
-            if (ok) {
-                TL xr = (TL)b[(size_t)r * ld + c] - acc;
-                if (!unit) xr = xr / d;
-                if (SF) {
-                    if (r != a.fault_row) publish<TX>(x + (size_t)r * ld + c, (TX)xr);
-                } else {
-                    x[(size_t)r * ld + c] = (TX)xr;
-                }
-            }
-        }
+    const int wib = threadIdx.x >> 5;
+    if (SF) {
+        for (int base; (base = sf_next_chunk(a.ticket, a.task_end)) >= 0;)
+            if (base + wib < a.task_end) trsm_task<TL, TB, TX, SF>(a, base + wib);
+        sf_finish(a.ticket);
+    } else {
+        const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
+        if (task < a.task_end) trsm_task<TL, TB, TX, SF>(a, task);
     }
-    if (SF) sf_finish(a.ticket);
 }
 
 template <class TL, class TB, class TX, bool SF>
-int launch(int vw, bool multi, int grid, cudaStream_t s, const TriArgs &a) {
+int launch(bool multi, int grid, cudaStream_t s, const TriArgs &a) {
     count_launch();
-    if (multi) {
-        k_trsm<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
-    } else {
-        switch (vw) {
-            case 1: k_trsv<TL, TB, TX, 1, SF><<<grid, kBlock, 0, s>>>(a); break;
-            case 2: k_trsv<TL, TB, TX, 2, SF><<<grid, kBlock, 0, s>>>(a); break;
-            case 4: k_trsv<TL, TB, TX, 4, SF><<<grid, kBlock, 0, s>>>(a); break;
-            case 8: k_trsv<TL, TB, TX, 8, SF><<<grid, kBlock, 0, s>>>(a); break;
-            case 16: k_trsv<TL, TB, TX, 16, SF><<<grid, kBlock, 0, s>>>(a); break;
-            default: k_trsv<TL, TB, TX, 32, SF><<<grid, kBlock, 0, s>>>(a); break;
-        }
-    }
+    if (multi) k_trsm<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
+    else k_trsv<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }
@@ -185,26 +327,28 @@ int launch(int vw, bool multi, int grid, cudaStream_t s, const TriArgs &a) {
 template <class TL, class TB, class TX>
 int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int nrhs) {
     const LevelSet &L = h->ls[structure];
+    const Bins &W = L.bins;
     cudaStream_t s = h->stream;
     TriArgs a{};
     switch (structure) {
         case JV_LOWER:
             a.beg = {h->rowptr, 0, 0}; a.end = {h->diag, 0, 0};
-            a.idx = h->colidx; a.vmap = nullptr; a.unit = 1; break;
+            a.idx = h->colidx; a.vmap = nullptr; a.unit = 1; a.reverse = 0; break;
         case JV_UPPER:
             a.beg = {h->diag, 0, 1}; a.end = {h->rowptr, 1, 0};
-            a.idx = h->colidx; a.vmap = nullptr; a.unit = 0; break;
+            a.idx = h->colidx; a.vmap = nullptr; a.unit = 0; a.reverse = 0; break;
         case JV_UPPER_T:
             a.beg = {h->colptr, 0, 0}; a.end = {h->cdiag, 0, 0};
-            a.idx = h->rowidx; a.vmap = h->csc2csr; a.unit = 0; break;
+            a.idx = h->rowidx; a.vmap = h->csc2csr; a.unit = 0; a.reverse = 0; break;
         default:  // JV_LOWER_T
             a.beg = {h->cdiag, 0, 1}; a.end = {h->colptr, 1, 0};
-            a.idx = h->rowidx; a.vmap = h->csc2csr; a.unit = 1; break;
+            a.idx = h->rowidx; a.vmap = h->csc2csr; a.unit = 1; a.reverse = 1; break;
     }
+    const bool multi = nrhs > 1;
     a.diag = h->diag;
-    a.rows = L.rows;
-    a.task_lo = L.task_lo;
-    a.task_hi = L.task_hi;
+    a.rows = multi ? L.rows : W.rows;
+    a.task_lo = W.task_lo;
+    a.task_hi = W.task_hi;
     a.lu = lu;
     a.b = b;
     a.x = x;
@@ -213,19 +357,19 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     a.status = h->status;
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
-    const bool multi = nrhs > 1;
+    a.backoff_ns = sf_backoff(h);
     if (h->opt.mode == JV_MODE_SYNCFREE) {
         int rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
         if (rc) return rc;
         a.task_begin = 0;
-        a.task_end = multi ? h->n : L.ntasks;
-        return launch<TL, TB, TX, true>(L.vw, multi, grid_for(a.task_end, kWarpsPerBlock), s, a);
+        a.task_end = multi ? h->n : W.ntasks;
+        return launch<TL, TB, TX, true>(multi, sf_grid(h, a.task_end), s, a);
     }
     for (int l = 0; l < L.nlev; ++l) {
-        a.task_begin = multi ? L.h_ptr[l] : L.h_task_ptr[l];
-        a.task_end = multi ? L.h_ptr[l + 1] : L.h_task_ptr[l + 1];
-        int rc = launch<TL, TB, TX, false>(L.vw, multi,
-                                           grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+        a.task_begin = multi ? L.h_ptr[l] : W.h_task_ptr[l];
+        a.task_end = multi ? L.h_ptr[l + 1] : W.h_task_ptr[l + 1];
+        int rc = launch<TL, TB, TX, false>(multi, grid_for(a.task_end - a.task_begin, kWarpsPerBlock),
+                                           s, a);
         if (rc) return rc;
     }
     return JV_OK;

@@ -60,12 +60,11 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False):
     oy = O.lsolve(rp, ci, diag, olu64, bb.astype(np.float64))
     oz = O.usolve(rp, ci, diag, olu64, oy)
     if dtype == np.float64:
-        assert close(y.cpu().numpy(), oy)[0]
-        assert close(z.cpu().numpy(), oz)[0]
+        assert np.array_equal(y.cpu().numpy(), oy)
+        assert np.array_equal(z.cpu().numpy(), oz)
         x = W.rhs(len(rp) - 1, 1, seed=21)
         s = jv.jv_spmv(h, T(v), T(x)).cpu().numpy()
-        scale = O.spmv(rp, ci, np.abs(v), np.abs(x))
-        assert np.all(np.abs(s - O.spmv(rp, ci, v, x)) <= 1e-12 * scale)
+        assert np.array_equal(s, O.spmv(rp, ci, v, x))
     else:
         assert max_rel(y.cpu().numpy(), oy) < 1e-4
         assert max_rel(z.cpu().numpy(), oz) < 1e-3
@@ -106,10 +105,10 @@ def test_c5_aniso_1024_32rhs():
     assert max_rel(y.cpu().numpy(), oy) < 1e-4 and max_rel(z.cpu().numpy(), oz) < 1e-3
     # FP64 32-RHS parity on the same factor
     y64 = jv.jv_lsolve(h, T(lu64), T(B))
-    assert close(y64.cpu().numpy(), O.lsolve(rp, ci, diag, lu64, B))[0]
+    assert np.array_equal(y64.cpu().numpy(), O.lsolve(rp, ci, diag, lu64, B))
     g = c["g"]
     gy = jv.jv_usolve_t(h, T(lu64), T(g)).cpu().numpy()
-    assert close(gy, O.usolve_t(rp, ci, diag, lu64, g))[0]
+    assert np.array_equal(gy, O.usolve_t(rp, ci, diag, lu64, g))
 
 
 @pytest.mark.slow
