@@ -229,6 +229,31 @@ int jv_fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu,
               const double *b, double *x, const jv_krylov_opts *o,
               jv_krylov_info *info);
 
+/* Forward substitution x = L^-1 b that allocates no device memory (the paper
+ * has no counterpart: this is a convenience for callers that cannot call
+ * cudaMalloc -- code running under an allocator or memory budget it does not
+ * own, code that must avoid the synchronisation cudaMalloc/cudaFree imply, or
+ * code with no place to keep a jv_handle).  Same arithmetic and result as
+ * jv_lsolve with FP64 factor and vectors and one right-hand side.
+ *   n <= 2097152 (2^21) rows, else JV_ERR_ARG (the scratch is fixed-size).
+ *   rowptr[n+1], colidx[], diag[n]: CSR pattern of the factor and the
+ *   position of every diagonal entry (e.g. from jv_get_pattern); lu[]: the
+ *   factor from jv_ilu0_factor; order[n]: the rows in an order in which every
+ *   row comes after all rows it depends on (the level sets of jv_get_levels
+ *   for JV_LOWER, or simply 0..n-1); b[n] in, x[n] out (x must not alias b).
+ *   stream: cudaStream_t (NULL = legacy default stream).  Synchronises the
+ *   stream and returns JV_OK or JV_ERR_TIMEOUT (a wait gave up: order is not
+ *   dependency-respecting).
+ * Its scratch (8 MB of per-row flags plus a few words) is one file-scope
+ * device array that every GPU loading the library holds until the process
+ * exits.  Its device address is looked up on the first call made on each
+ * device, so make that first call before any stream capture.  All calls share
+ * the array and each call clears it before use, so calls that overlap on the
+ * GPU race. */
+int jv_lsolve_noalloc(int n, const int *rowptr, const int *colidx, const int *diag,
+                      const int *order, const double *lu, const double *b, double *x,
+                      void *stream);
+
 /* Number of kernels this library has launched in the process so far. */
 unsigned long long jv_launch_count(void);
 

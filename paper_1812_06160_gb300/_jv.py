@@ -95,6 +95,7 @@ _SIGS = {
                     ctypes.POINTER(jv_krylov_info)]),
     "jv_fgmres": (_i, [_v, _v, _i, _v, _v, _v, ctypes.POINTER(jv_krylov_opts),
                        ctypes.POINTER(jv_krylov_info)]),
+    "jv_lsolve_noalloc": (_i, [_i, _v, _v, _v, _v, _v, _v, _v, _v]),
     "jv_launch_count": (ctypes.c_ulonglong, []),
     "jv_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -406,6 +407,22 @@ def jv_pcg(h, vals, lu, b, x=None, tol=1e-8, maxit=10000):
 def jv_fgmres(h, vals, lu, b, x=None, tol=1e-8, restart=30, max_restarts=200):
     """Right-preconditioned FGMRES(restart) in FP64 with the factor ``lu``."""
     return _krylov("jv_fgmres", h, vals, lu, b, x, tol, None, restart, max_restarts)
+
+
+def jv_lsolve_noalloc(rowptr, colidx, diag, order, lu, b, x=None):
+    """x = L^-1 b (FP64, one right-hand side) without any device allocation
+    by the library; see include/jv.h.  All arguments are CUDA tensors."""
+    n = rowptr.numel() - 1
+    if x is None:
+        x = torch.empty_like(b)
+    st = lib.jv_lsolve_noalloc(
+        n, _dev(rowptr, "rowptr", dtype=torch.int32), _dev(colidx, "colidx", dtype=torch.int32),
+        _dev(diag, "diag", numel=n, dtype=torch.int32), _dev(order, "order", numel=n, dtype=torch.int32),
+        _dev(lu, "lu", dtype=torch.float64), _dev(b, "b", numel=n, dtype=torch.float64),
+        _dev(x, "x", numel=n, dtype=torch.float64),
+        ctypes.c_void_p(torch.cuda.current_stream(b.device).cuda_stream))
+    _check("jv_lsolve_noalloc", st)
+    return x
 
 
 def jv_launch_count() -> int:
