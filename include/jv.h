@@ -84,6 +84,10 @@ typedef struct {
                                        0 = default */
     int sf_backoff_ns;              /* longest pause between two polls of a value that is not
                                        ready; 0 = default, negative = never pause */
+    int band_rows;                  /* sync-free band schedule: rows per band (> 0), one CTA
+                                       per band, local levels inside it.  0 or -1 = the
+                                       level-ordered schedule (the default: on GB300 it is
+                                       the faster one for every workload measured) */
 } jv_options;
 
 typedef struct {
@@ -92,6 +96,9 @@ typedef struct {
     int nlev[4];                /* levels per jv_structure */
     int nlong[4];               /* rows run one per warp, per jv_structure */
     int nlong_factor;           /* rows the factor runs one per warp */
+    int band_rows[4];           /* band size per jv_structure, 0 when the band schedule
+                                   is not used for it */
+    int nband_levels[4];        /* local levels over all bands */
     long long npairs;           /* update pairs of the symbolic factorisation (flops of the
                                    factor = 2 npairs + nnz_lower) */
     int mode, reorder;

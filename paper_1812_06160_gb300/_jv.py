@@ -38,13 +38,15 @@ class jv_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("reorder", ctypes.c_int), ("check", ctypes.c_int),
                 ("long_row", ctypes.c_int),
                 ("spin_timeout_cycles", ctypes.c_longlong), ("fault_row", ctypes.c_int),
-                ("sf_ctas_per_sm", ctypes.c_int), ("sf_backoff_ns", ctypes.c_int)]
+                ("sf_ctas_per_sm", ctypes.c_int), ("sf_backoff_ns", ctypes.c_int),
+                ("band_rows", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_int), ("nnz_lower", ctypes.c_int),
                 ("nnz_upper", ctypes.c_int), ("nlev", ctypes.c_int * 4),
                 ("nlong", ctypes.c_int * 4), ("nlong_factor", ctypes.c_int),
+                ("band_rows", ctypes.c_int * 4), ("nband_levels", ctypes.c_int * 4),
                 ("npairs", ctypes.c_longlong), ("mode", ctypes.c_int), ("reorder", ctypes.c_int)]
 
 
@@ -183,7 +185,8 @@ class Handle:
 
 
 def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_row=0,
-               spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0):
+               spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0,
+               band_rows=0):
     """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle."""
     n = rowptr.numel() - 1
     nnz = colidx.numel()
@@ -199,6 +202,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
     opt.fault_row = int(fault_row)
     opt.sf_ctas_per_sm = int(sf_ctas_per_sm)
     opt.sf_backoff_ns = int(sf_backoff_ns)
+    opt.band_rows = int(band_rows)
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):
@@ -320,6 +324,7 @@ def jv_get_info(h):
     _check("jv_get_info", lib.jv_get_info(h.ptr, ctypes.byref(info)))
     return dict(n=info.n, nnz=info.nnz, nnz_lower=info.nnz_lower, nnz_upper=info.nnz_upper,
                 nlev=list(info.nlev), nlong=list(info.nlong), nlong_factor=info.nlong_factor,
+                band_rows=list(info.band_rows), nband_levels=list(info.nband_levels),
                 npairs=info.npairs, mode=info.mode, reorder=info.reorder)
 
 

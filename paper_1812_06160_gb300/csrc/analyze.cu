@@ -438,7 +438,7 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     for (int k = 0; k < 4; ++k)
         JV_TRY(make_bins(h, h->ls[k], cost.data() + (size_t)k * n, long_deps, h->ls[k].bins));
     JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, kLaneSlot, h->fbins));
-    return JV_OK;
+    return plan_bands(h);
 }
 
 // ------------------------------------------------------------- reordering

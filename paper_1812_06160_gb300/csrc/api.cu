@@ -231,6 +231,10 @@ int jv_get_info(jv_handle h, jv_info *info) {
         info->nlong[k] = h->ls[k].bins.nlong;
     }
     info->nlong_factor = h->fbins.nlong;
+    for (int k = 0; k < 4; ++k) {
+        info->band_rows[k] = h->ls[k].band.use ? h->ls[k].band.B : 0;
+        info->nband_levels[k] = h->ls[k].band.use ? h->ls[k].band.nll_total : 0;
+    }
     info->npairs = h->npairs;
     info->mode = h->opt.mode;
     info->reorder = h->opt.reorder;

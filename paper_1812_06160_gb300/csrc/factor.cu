@@ -368,6 +368,9 @@ int run(jv_handle h, const void *vals, void *lu) {
         JV_CUDA(cudaMemcpyAsync(copy, vals, (size_t)h->nnz * sizeof(TV), cudaMemcpyDeviceToDevice, s));
         vals = copy;
     }
+    if (h->opt.mode == JV_MODE_SYNCFREE && L.band.use)
+        return band_factor(h, sizeof(TV) == 8 ? JV_F64 : JV_F32, vals,
+                           sizeof(TL) == 8 ? JV_F64 : JV_F32, lu, h->fscratch);
     FactorArgs a;
     a.rowptr = h->rowptr;
     a.diag = h->diag;

@@ -200,6 +200,25 @@ struct Bins {
     std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
 };
 
+// Band schedule of one level structure: rows split into nb contiguous bands
+// of B rows (natural order); inside a band, rows are grouped by their local
+// level -- the longest path through dependencies that stay inside the band.
+// One CTA runs a band: local levels in order, separated by __syncthreads,
+// values of the band's rows kept in shared memory; dependencies on other
+// bands are awaited on the published output words.  Bands are claimed in
+// dependency order (ascending for forward structures, descending for
+// backward ones), so a band only waits on bands claimed before it.
+struct BandPlan {
+    bool use = false;
+    int B = 0, nb = 0;
+    int nll_total = 0;         // local levels over all bands
+    int nll_max = 0;
+    double internal_frac = 0;  // dependencies inside their band / all dependencies
+    int *bl_ptr = nullptr;     // [nb+1] first local level of every band
+    int *ll_ptr = nullptr;     // [nll_total+1] first position in rows of every local level
+    int *rows = nullptr;       // [n] rows by (band, local level, row)
+};
+
 struct LevelSet {
     int nlev = 0;
     int *lev = nullptr;        // [n] level of every row
@@ -207,6 +226,7 @@ struct LevelSet {
     int *rows = nullptr;       // [n] rows grouped by level, ascending inside
     std::vector<int> h_ptr;    // host copy of ptr
     Bins bins;                 // single right-hand-side solve work list
+    BandPlan band;
 };
 
 struct Workspace;  // Krylov scratch, krylov.cu
@@ -289,6 +309,13 @@ int analyze(jv_handle h, const int *rowptr, const int *colidx);
 
 // factor.cu
 int ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu);
+
+// band.cu: band schedule planner (host) and the band kernels
+int plan_bands(jv_handle h);
+int band_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,
+               const void *b, jv_dtype x_t, void *x);
+int band_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu,
+                void *scratch);
 
 // trisolve.cu
 int tri_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,

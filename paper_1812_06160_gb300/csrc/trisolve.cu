@@ -324,9 +324,13 @@ int launch(bool multi, int grid, cudaStream_t s, const TriArgs &a) {
     return JV_OK;
 }
 
+template <class T> constexpr jv_dtype dt() { return sizeof(T) == 8 ? JV_F64 : JV_F32; }
+
 template <class TL, class TB, class TX>
 int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int nrhs) {
     const LevelSet &L = h->ls[structure];
+    if (h->opt.mode == JV_MODE_SYNCFREE && nrhs == 1 && L.band.use)
+        return band_solve(h, structure, dt<TL>(), lu, dt<TB>(), b, dt<TX>(), x);
     const Bins &W = L.bins;
     cudaStream_t s = h->stream;
     TriArgs a{};

@@ -4,6 +4,23 @@ import numpy as np
 import workloads as W
 
 
+SCHEDULES = ("level", "syncfree", "band")
+
+
+def analyze(jv, rowptr, colidx, schedule, **kw):
+    """Handle for one schedule: 'level' (one launch per level), 'syncfree'
+    (one persistent launch over level-ordered tasks), 'band' (sync-free band
+    schedule, forced with a small band so it meets every pattern)."""
+    import torch
+    rp = torch.tensor(np.asarray(rowptr), device="cuda")
+    ci = torch.tensor(np.asarray(colidx), device="cuda")
+    if schedule == "level":
+        return jv.jv_analyze(rp, ci, mode="level", **kw)
+    if schedule == "syncfree":
+        return jv.jv_analyze(rp, ci, mode="syncfree", band_rows=-1, **kw)
+    return jv.jv_analyze(rp, ci, mode="syncfree", band_rows=kw.pop("band_rows", 64), **kw)
+
+
 def close(got, want, rel=1e-12, floor_frac=1e-6):
     """Per-entry bound |g - o| <= rel * max(|o|, floor_frac * max|o|): relative
     error per entry, with a floor for entries that cancelled to near zero

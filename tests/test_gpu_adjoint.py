@@ -7,7 +7,7 @@ import torch
 
 import oracle as O
 import workloads as W
-from jvutil import max_rel
+from jvutil import SCHEDULES, analyze, max_rel
 
 jv = pytest.importorskip("paper_1812_06160_gb300")
 pytestmark = pytest.mark.gpu
@@ -27,13 +27,13 @@ def _oracle_adjoint(rp, ci, lu, r, gz):
     return z, gr, g
 
 
-@pytest.mark.parametrize("mode", ["level", "syncfree"])
+@pytest.mark.parametrize("mode", SCHEDULES)
 def test_backward_matches_oracle_adjoint(mode):
     rp, ci, v = W.aniso5(20)
     n = len(rp) - 1
     olu, _, _ = O.ilu0(rp, ci, v)
     r, gz = W.rhs(n, 6, seed=1), W.rhs(n, 6, seed=2)
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     rt = T(r, requires_grad=True)
     lut = T(olu, requires_grad=True)
     z = jv.ilu_apply(rt, lut, h)

@@ -9,7 +9,7 @@ import torch
 
 import oracle as O
 import workloads as W
-from jvutil import close, max_rel
+from jvutil import analyze, max_rel
 
 jv = pytest.importorskip("paper_1812_06160_gb300")
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,10 @@ def _levels_match(h, rp, ci):
 
 
 def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False):
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode, reorder=reorder)
+    if mode == "auto":        # the benchmark's configuration: sync-free, schedule chosen by the analysis
+        h = jv.jv_analyze(T(rp), T(ci), reorder=reorder)
+    else:
+        h = analyze(jv, rp, ci, mode, reorder=reorder)
     if reorder:
         _, _, _, perm = O.level_sets(rp, ci)
         _, rp, ci, vmap = O.permute(rp, ci, perm)
@@ -71,7 +74,7 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False):
     return h
 
 
-@pytest.mark.parametrize("mode", ["syncfree", "level"])
+@pytest.mark.parametrize("mode", ["auto", "syncfree", "level"])
 def test_c2_lap7_128_fp64(mode):
     c = cfg("c2")
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], mode)
@@ -79,13 +82,13 @@ def test_c2_lap7_128_fp64(mode):
 
 def test_c2_lap7_128_fp64_reordered():
     c = cfg("c2")
-    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "syncfree", reorder=True)
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", reorder=True)
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_c3_cd27_96(dtype):
     c = cfg("c3")
-    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "syncfree", dtype=dtype)
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", dtype=dtype)
 
 
 def test_c5_aniso_1024_32rhs():
@@ -114,5 +117,5 @@ def test_c5_aniso_1024_32rhs():
 @pytest.mark.slow
 def test_c4_powerlaw_1e6():
     c = cfg("c4")
-    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "syncfree")
-    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "syncfree", dtype=np.float32)
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto")
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", dtype=np.float32)

@@ -9,6 +9,7 @@ import torch
 
 import oracle as O
 import workloads as W
+from jvutil import SCHEDULES, analyze
 
 jv = pytest.importorskip("paper_1812_06160_gb300")
 pytestmark = pytest.mark.gpu
@@ -18,14 +19,14 @@ def T(a):
     return torch.tensor(np.asarray(a), device="cuda")
 
 
-@pytest.mark.parametrize("mode", ["level", "syncfree"])
+@pytest.mark.parametrize("mode", SCHEDULES)
 def test_zero_pivot_row_matches_oracle(mode):
     rp = np.array([0, 2, 5, 7], dtype=np.int32)
     ci = np.array([0, 1, 0, 1, 2, 1, 2], dtype=np.int32)
     v = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 3.0])
     _, st, bad = O.ilu0(rp, ci, v)
     assert st == O.ERR_ZERO_PIVOT and bad == 1
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     with pytest.raises(jv.JvError) as e:
         jv.jv_ilu0_factor(h, T(v))
     assert e.value.status == jv.JV_ERR_ZERO_PIVOT and e.value.bad_row == 1
@@ -38,19 +39,21 @@ def test_zero_pivot_in_large_matrix():
     v2[rp[777]:diag[777] + 1] = 0.0          # no multipliers and a zero diagonal: u_777 == 0
     _, st2, bad2 = O.ilu0(rp, ci, v2)
     assert st2 == O.ERR_ZERO_PIVOT and bad2 == 777
-    for mode in ("level", "syncfree"):
-        h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    for mode in SCHEDULES:
+        h = analyze(jv, rp, ci, mode)
         with pytest.raises(jv.JvError) as e:
             jv.jv_ilu0_factor(h, T(v2))
         assert e.value.status == jv.JV_ERR_ZERO_PIVOT and e.value.bad_row == bad2
 
 
-def test_syncfree_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("mode", ["syncfree", "band"])
+def test_syncfree_timeout_is_reported_and_context_survives(mode):
     rp, ci, v = W.lap5(24)
     n = len(rp) - 1
-    fault = 100
-    h = jv.jv_analyze(T(rp), T(ci), mode="syncfree", fault_row=fault,
-                      spin_timeout_cycles=2_000_000)
+    # the last row of a 64-row band: every row that depends on it lies in the
+    # next band, so in both sync-free schedules its dependants await it
+    fault = 127
+    h = analyze(jv, rp, ci, mode, fault_row=fault, spin_timeout_cycles=2_000_000)
     with pytest.raises(jv.JvError) as e:
         jv.jv_ilu0_factor(h, T(v))
     assert e.value.status == jv.JV_ERR_TIMEOUT and e.value.bad_row > fault
@@ -62,7 +65,7 @@ def test_syncfree_timeout_is_reported_and_context_survives():
         jv.jv_lsolve(h, T(olu), T(W.rhs(n, 4, seed=1)))
     assert e.value.status == jv.JV_ERR_TIMEOUT
     # the device is still healthy: a clean handle factors bit-exactly
-    h2 = jv.jv_analyze(T(rp), T(ci), mode="syncfree")
+    h2 = analyze(jv, rp, ci, mode)
     assert np.array_equal(jv.jv_ilu0_factor(h2, T(v)).cpu().numpy(), olu)
     torch.cuda.synchronize()
 

@@ -9,6 +9,7 @@ import torch
 
 import oracle as O
 import workloads as W
+from jvutil import SCHEDULES, analyze
 
 jv = pytest.importorskip("paper_1812_06160_gb300")
 pytestmark = pytest.mark.gpu
@@ -18,13 +19,13 @@ def T(a):
     return torch.tensor(np.asarray(a), device="cuda")
 
 
-@pytest.mark.parametrize("mode", ["level", "syncfree"])
+@pytest.mark.parametrize("mode", SCHEDULES)
 def test_pcg_matches_oracle(mode):
     c = W.config("c1")
     rp, ci, v, b = c["rowptr"], c["colidx"], c["vals"], c["b"]
     olu, _, _ = O.ilu0(rp, ci, v)
     ox, oit, orel = O.pcg(rp, ci, v, olu, b, tol=1e-8)
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     vt = T(v)
     lu = jv.jv_ilu0_factor(h, vt)
     x, info = jv.jv_pcg(h, vt, lu, T(b), tol=1e-8)
@@ -37,7 +38,7 @@ def test_pcg_matches_oracle(mode):
     assert abs(info32["iters"] - oit) <= 3
 
 
-@pytest.mark.parametrize("mode", ["level", "syncfree"])
+@pytest.mark.parametrize("mode", SCHEDULES)
 def test_fgmres_matches_oracle(mode):
     rp, ci, v, _ = W.cd27(10)
     n = len(rp) - 1
@@ -45,7 +46,7 @@ def test_fgmres_matches_oracle(mode):
     olu, _, _ = O.ilu0(rp, ci, v)
     ox, oit, orel = O.fgmres(rp, ci, v, olu, b, m=30, tol=1e-8)
     assert oit > 0
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     vt = T(v)
     lu = jv.jv_ilu0_factor(h, vt)
     x, info = jv.jv_fgmres(h, vt, lu, T(b), tol=1e-8, restart=30)

@@ -11,14 +11,14 @@ import torch
 
 import oracle as O
 import workloads as W
-from jvutil import close, max_rel, small_matrices
+from jvutil import SCHEDULES, analyze, close, max_rel, small_matrices
 
 jv = pytest.importorskip("paper_1812_06160_gb300")
 pytestmark = pytest.mark.gpu
 
 CASES = small_matrices()
 IDS = [c[0] for c in CASES]
-MODES = ["level", "syncfree"]
+MODES = list(SCHEDULES)
 
 
 def T(a):
@@ -29,7 +29,7 @@ def T(a):
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_factor_fp64_bit_exact(case, mode):
     _, rp, ci, v = case
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     lu = jv.jv_ilu0_factor(h, T(v))
     olu, st, _ = O.ilu0(rp, ci, v)
     assert st == 0
@@ -40,7 +40,7 @@ def test_factor_fp64_bit_exact(case, mode):
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_factor_fp32_bit_exact_to_fp32_twin(case, mode):
     _, rp, ci, v = case
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     olu32, st, _ = O.ilu0(rp, ci, v.astype(np.float32), dtype=np.float32)
     lu = jv.jv_ilu0_factor(h, T(v), lu_dtype=torch.float32)        # fused down-cast
     assert np.array_equal(lu.cpu().numpy(), olu32)
@@ -58,7 +58,7 @@ def test_factor_fp32_bit_exact_to_fp32_twin(case, mode):
 def test_solves_fp64(case, nrhs, mode):
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     olu, _, _ = O.ilu0(rp, ci, v)
     diag = O.diag_ptr(rp, ci)
     b = W.rhs(n, nrhs, seed=7 + nrhs)
@@ -76,7 +76,7 @@ def test_solves_fp64(case, nrhs, mode):
 def test_solves_fp32_and_mixed(case, mode):
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), mode=mode)
+    h = analyze(jv, rp, ci, mode)
     olu32, _, _ = O.ilu0(rp, ci, v.astype(np.float32), dtype=np.float32)
     diag = O.diag_ptr(rp, ci)
     lu64 = olu32.astype(np.float64)
