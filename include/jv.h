@@ -261,6 +261,20 @@ int jv_lsolve_noalloc(int n, const int *rowptr, const int *colidx, const int *di
                       const int *order, const double *lu, const double *b, double *x,
                       void *stream);
 
+/* Measured latency of one dependency hop, in microseconds: a value stored by
+ * one SM (relaxed store, gpu scope) and seen by another SM polling it
+ * (relaxed load).  In the point-to-point schedule of Sec. III-A (Fig. 4)
+ * every level of the dependency DAG costs at least one such hop, so
+ * levels x hop is the critical-path bound of the sync-free kernels.
+ * Launches a cooperative grid of one 32-thread CTA per SM on `stream`
+ * (cudaStream_t or NULL) in which CTA 0 and a partner CTA exchange `rounds`
+ * round trips (> 0); repeated for `npartners` (> 0) partners spread over the
+ * grid (both dies); *out_us (host) receives the median one-way time.
+ * Synchronous; allocates and frees 272 bytes of device memory.  Every wait
+ * is bounded (0.2 s per partner): JV_ERR_TIMEOUT if one expired,
+ * JV_ERR_CUDA if cooperative launch is unsupported or a CUDA call failed. */
+int jv_hop_latency(int rounds, int npartners, double *out_us, void *stream);
+
 /* Number of kernels this library has launched in the process so far. */
 unsigned long long jv_launch_count(void);
 

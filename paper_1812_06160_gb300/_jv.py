@@ -98,6 +98,7 @@ _SIGS = {
     "jv_fgmres": (_i, [_v, _v, _i, _v, _v, _v, ctypes.POINTER(jv_krylov_opts),
                        ctypes.POINTER(jv_krylov_info)]),
     "jv_lsolve_noalloc": (_i, [_i, _v, _v, _v, _v, _v, _v, _v, _v]),
+    "jv_hop_latency": (_i, [_i, _i, ctypes.POINTER(ctypes.c_double), _v]),
     "jv_launch_count": (ctypes.c_ulonglong, []),
     "jv_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -428,6 +429,16 @@ def jv_lsolve_noalloc(rowptr, colidx, diag, order, lu, b, x=None):
         ctypes.c_void_p(torch.cuda.current_stream(b.device).cuda_stream))
     _check("jv_lsolve_noalloc", st)
     return x
+
+
+def jv_hop_latency(rounds=1000, npartners=16, device=None) -> float:
+    """Median one-way latency (microseconds) of a value published by one SM
+    and polled by another: the unit step of the sync-free critical path."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    out = ctypes.c_double(0.0)
+    _check("jv_hop_latency", lib.jv_hop_latency(int(rounds), int(npartners), ctypes.byref(out),
+                                                ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+    return out.value
 
 
 def jv_launch_count() -> int:

@@ -310,6 +310,11 @@ int jv_fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu, co
     return jv::fgmres(h, vals, lu_t, lu, b, x, o ? o : &d, info);
 }
 
+int jv_hop_latency(int rounds, int npartners, double *out_us, void *stream) {
+    if (rounds <= 0 || npartners <= 0 || !out_us) return JV_ERR_ARG;
+    return jv::hop_latency(rounds, npartners, out_us, static_cast<cudaStream_t>(stream));
+}
+
 unsigned long long jv_launch_count(void) { return jv::g_launches.load(); }
 
 const char *jv_status_string(int status) {

@@ -106,12 +106,13 @@ __device__ __forceinline__ typename Bits<T>::U first_read(const T *p) {
 template <class T>
 __device__ __forceinline__ void publish(T *p, T v) {
     using B = Bits<T>;
-    typename B::U u = isnan(v) ? B::kCanonNan : B::to(v);
-    st_relaxed(reinterpret_cast<typename B::U *>(p), u);
+    typename B::U u = B::to(v);
+    st_relaxed(reinterpret_cast<typename B::U *>(p), B::nan_bits(u) ? B::kCanonNan : u);
 }
 
-__device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, double d) {
-    if (d == 0.0 || !isfinite(d)) report(a.status, JV_ERR_ZERO_PIVOT, r);
+template <class T>
+__device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, T d) {
+    if (Bits<T>::zero_or_nonfinite_bits(Bits<T>::to(d))) report(a.status, JV_ERR_ZERO_PIVOT, r);
 }
 
 // ------------------------------------------------------- one lane per row
@@ -195,7 +196,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                 }
                 V(p) = lik;
             }
-            pivot_check(a, r, (double)V(nl));
+            pivot_check<TL>(a, r, V(nl));
             for (int e = 0; e < len; ++e) {
                 if (!SF || e < nl) lu[rs + e] = V(e);
                 else if (r != a.fault_row) publish<TL>(lu + rs + e, V(e));
@@ -289,7 +290,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         if (lane == 0) w[p] = lik;
     }
     __syncwarp();
-    if (lane == 0) pivot_check(a, r, (double)w[nl]);
+    if (lane == 0) pivot_check<TL>(a, r, w[nl]);
     for (int e = lane; e < len; e += kWarp) {
         const TL v = w[e];
         if (!SF || e < nl) lu[rs + e] = v;
@@ -307,13 +308,13 @@ __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsig
 }
 
 template <class TV, class TL, bool SF>
-__global__ void __launch_bounds__(kBlock) k_ilu0(FactorArgs a) {
+__global__ void __launch_bounds__(kBlock, 1) k_ilu0(FactorArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int wib = threadIdx.x >> 5;
     unsigned char *smem = dyn_smem + (size_t)wib * kWarpSmem;
     if (SF) {
-        for (int base; (base = sf_next_chunk(a.ticket, a.task_end)) >= 0;)
-            if (base + wib < a.task_end) factor_task<TV, TL, SF>(a, base + wib, smem);
+        sf_for_each_task(a.ticket, a.task_end,
+                         [&](int task) { factor_task<TV, TL, SF>(a, task, smem); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;

@@ -111,6 +111,8 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
 // fault costs one timeout period.
 //
 // Returns the first task of the CTA's next chunk, or -1 (block-uniform).
+// (Used by the allocation-free solve; the kernels of the handle claim per
+// warp, see sf_for_each_task.)
 __device__ __forceinline__ int sf_next_chunk(unsigned *ticket, int ntasks) {
     __shared__ int s_base;
     __syncthreads();
@@ -125,6 +127,31 @@ __device__ __forceinline__ void sf_pause(unsigned it, unsigned max_ns) {
     unsigned ns = 16u << min(it - 4u, 6u);
     __nanosleep(ns < max_ns ? ns : max_ns);
 }
+// Per-warp claims: every warp takes the next level-ordered task with one
+// atomic of its lane 0, so the consecutive tasks of one level spread over
+// the warps of all SMs (a CTA-sized chunk would put a whole slice of the
+// level on one SM, whose FP64 units and load path then set the pace of the
+// level).  The claim for the warp's next task is issued when the current
+// task starts and read when it ends, so its latency hides behind the task.
+// Every task waits only on tasks of lower index, each claimed by a resident
+// warp (a warp's pending claim is above its current task), so the lowest
+// unfinished task always runs: no deadlock.  Warp-uniform; lanes must be
+// converged.
+template <class F>
+__device__ __forceinline__ void sf_for_each_task(unsigned *ticket, int ntasks, F &&run) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    unsigned claim = 0;
+    if (lane == 0) claim = atomicAdd(ticket, 1u);
+    int task = __shfl_sync(0xffffffffu, (int)claim, 0);
+    while (task < ntasks) {
+        unsigned next = 0;
+        if (lane == 0) next = atomicAdd(ticket, 1u);
+        run(task);
+        __syncwarp();
+        task = __shfl_sync(0xffffffffu, (int)next, 0);
+    }
+}
+
 __device__ __forceinline__ void sf_finish(unsigned *ticket) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -156,6 +183,11 @@ template <> struct Bits<double> {
     static constexpr U kCanonNan = 0x7ff8000000000000ull;
     __device__ static double from(U u) { return __longlong_as_double((long long)u); }
     __device__ static U to(double d) { return (U)__double_as_longlong(d); }
+    // integer tests: no FP64 instruction (the FP64 pipe is narrow on this part)
+    __device__ static bool nan_bits(U u) { return (u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull; }
+    __device__ static bool zero_or_nonfinite_bits(U u) {
+        return (u & 0x7fffffffffffffffull) == 0 || (u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+    }
 };
 template <> struct Bits<float> {
     using U = unsigned;
@@ -163,6 +195,10 @@ template <> struct Bits<float> {
     static constexpr U kCanonNan = 0x7fc00000u;
     __device__ static float from(U u) { return __uint_as_float(u); }
     __device__ static U to(float f) { return __float_as_uint(f); }
+    __device__ static bool nan_bits(U u) { return (u & 0x7fffffffu) > 0x7f800000u; }
+    __device__ static bool zero_or_nonfinite_bits(U u) {
+        return (u & 0x7fffffffu) == 0 || (u & 0x7f800000u) == 0x7f800000u;
+    }
 };
 
 // f(i) = a[i + ai] + ad: one kernel can walk a CSR or CSC sub-range of row or
@@ -318,6 +354,7 @@ int band_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, v
                 void *scratch);
 
 // trisolve.cu
+int hop_latency(int rounds, int npartners, double *out_us, cudaStream_t s);
 int tri_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,
               const void *b, jv_dtype x_t, void *x, int nrhs);
 

@@ -89,8 +89,8 @@ __device__ __forceinline__ typename Bits<TX>::U settle(const TX *p, typename Bit
 template <class TX>
 __device__ __forceinline__ void publish(TX *p, TX v) {
     using B = Bits<TX>;
-    typename B::U u = isnan(v) ? B::kCanonNan : B::to(v);
-    st_relaxed(reinterpret_cast<typename B::U *>(p), u);
+    typename B::U u = B::to(v);
+    st_relaxed(reinterpret_cast<typename B::U *>(p), B::nan_bits(u) ? B::kCanonNan : u);
 }
 
 template <class TX, bool SF>
@@ -140,9 +140,12 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     U u[kPoll];
     long long t0 = 0;
     unsigned rounds = 0;
+    // The loop body is warp-uniform (finished lanes only mask their work),
+    // so the consume step -- FP64 fused multiply-adds, slow on this part's
+    // narrow FP64 pipe even when predicated off -- is skipped outright in
+    // the common round where no lane's next dependency has arrived.
     while (__any_sync(0xffffffffu, !done)) {
-        if (done) continue;
-        if (e == wend) {
+        if (!done && e == wend && e < len) {
             // next window [wb, wend): indices, values and a first read of every x
             wb = e;
             wend = min(e + kPoll, len);
@@ -156,25 +159,32 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         }
         // (re-)read every entry of the window not consumed yet; dependencies
         // tend to arrive together, so they are all polled in the same round
+        bool progress = !done && e == len;
 #pragma unroll
         for (int k = 0; k < kPoll; ++k)
-            if (wb + k >= e && wb + k < wend) u[k] = first_read<TX, SF>(x + jw[k]);
-        // consume the ready prefix, in order
-        bool ok = true;
+            if (!done && wb + k >= e && wb + k < wend) {
+                u[k] = first_read<TX, SF>(x + jw[k]);
+                if (wb + k == e) progress = !SF || u[k] != B::kSent;
+            }
+        if (__any_sync(0xffffffffu, progress) && !done) {
+            // consume the ready prefix, in order
+            bool ok = true;
 #pragma unroll
-        for (int k = 0; k < kPoll; ++k) {
-            if (wb + k < e) continue;
-            if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
-                s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
-                ++e;
-            } else {
-                ok = false;
+            for (int k = 0; k < kPoll; ++k) {
+                if (wb + k < e) continue;
+                if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
+                    s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                    ++e;
+                } else {
+                    ok = false;
+                }
+            }
+            if (e == len) {
+                store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+                done = true;
             }
         }
-        if (e == len) {
-            store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
-            done = true;
-        } else if (SF && e < wend) {
+        if (SF && !done && !progress) {
             if (rounds++ == 0) t0 = clock64();
             if ((rounds & 15u) == 0) {
                 if (sf_aborted(a.ticket) || clock64() - t0 > a.timeout) {
@@ -248,8 +258,7 @@ template <class TL, class TB, class TX, bool SF>
 __global__ void __launch_bounds__(kBlock) k_trsv(TriArgs a) {
     const int wib = threadIdx.x >> 5;
     if (SF) {
-        for (int base; (base = sf_next_chunk(a.ticket, a.task_end)) >= 0;)
-            if (base + wib < a.task_end) trsv_task<TL, TB, TX, SF>(a, base + wib);
+        sf_for_each_task(a.ticket, a.task_end, [&](int task) { trsv_task<TL, TB, TX, SF>(a, task); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
@@ -306,8 +315,7 @@ template <class TL, class TB, class TX, bool SF>
 __global__ void __launch_bounds__(kBlock) k_trsm(TriArgs a) {
     const int wib = threadIdx.x >> 5;
     if (SF) {
-        for (int base; (base = sf_next_chunk(a.ticket, a.task_end)) >= 0;)
-            if (base + wib < a.task_end) trsm_task<TL, TB, TX, SF>(a, base + wib);
+        sf_for_each_task(a.ticket, a.task_end, [&](int task) { trsm_task<TL, TB, TX, SF>(a, task); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;

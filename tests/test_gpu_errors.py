@@ -93,3 +93,10 @@ def test_host_argument_errors():
     assert e.value.status == jv.JV_ERR_ARG
     with pytest.raises(TypeError):
         jv.jv_ilu0_factor(h, T(v).to(torch.int64))
+
+
+def test_hop_latency_probe():
+    # one publication seen by another SM: well under 10 us on any GPU this
+    # library targets, and never zero
+    hop = jv.jv_hop_latency(rounds=200, npartners=4)
+    assert 0.05 < hop < 10.0
