@@ -46,16 +46,24 @@ METRIC = "ILU(0) factor + stri + spmv GB/s (% HBM peak)"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 
-# ncu DRAM traffic (read + write bytes) per launch of the dominant kernel on
-# this workload, with the hash of the kernel source it was captured from; a
-# changed source makes the number stale and it is reported as null.
-TRAFFIC = {}
+# ncu DRAM traffic (read + write bytes) per launch of the dominant kernel,
+# keyed by (config, dtype, kernel, mode, reorder), with a hash of the kernel
+# sources it was captured from; a changed source makes the number stale and
+# it is reported as null.
+KERNEL_SOURCES = {"factor": ("factor.cu", "jv_internal.cuh"),
+                  "lsolve": ("trisolve.cu", "jv_internal.cuh"),
+                  "usolve": ("trisolve.cu", "jv_internal.cuh")}
+TRAFFIC = {
+    ("c2", "f64", "factor", "syncfree", False): (528_861_184, "211a77e53553"),
+}
 
 
-def _src_hash(fname):
-    p = os.path.join(ROOT, "paper_1812_06160_gb300", "csrc", fname)
-    with open(p, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+def _src_hash(fnames):
+    h = hashlib.sha1()
+    for fname in fnames:
+        with open(os.path.join(ROOT, "paper_1812_06160_gb300", "csrc", fname), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def byte_model(n, nnz, nnzl, nnzu, v, nrhs=1, adjoint=False):
@@ -377,7 +385,8 @@ def main(argv=None):
     peak, peak_kind = measured_peaks()
     achieved = model[dom] / (avg[dom] * 1e-3) / 1e9
     tr = TRAFFIC.get((a.config, a.dtype, dom, a.mode, a.reorder))
-    traffic = tr[0] if tr and tr[1] == _src_hash(tr[2]) else None
+    traffic = tr[0] if tr and dom in KERNEL_SOURCES and tr[1] == _src_hash(KERNEL_SOURCES[dom]) \
+        else None
     kern = {}
     for k in kernels:
         gbs = model[k] / (avg[k] * 1e-3) / 1e9

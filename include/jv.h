@@ -88,6 +88,11 @@ typedef struct {
                                        per band, local levels inside it.  0 or -1 = the
                                        level-ordered schedule (the default: on GB300 it is
                                        the faster one for every workload measured) */
+    int sf_gate_levels;             /* sync-free factor's level gate: a task polls its operands
+                                       only once the tasks of all levels below (its level -
+                                       this) have finished, sleeping until then; 0 = poll from
+                                       the start.  Default 1.  (The solves do not gate: on
+                                       GB300 it slowed them.) */
 } jv_options;
 
 typedef struct {

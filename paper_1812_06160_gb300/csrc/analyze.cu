@@ -308,9 +308,17 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, Bi
     }
     B.ntasks = (int)lo.size();
     B.h_task_ptr[L.nlev] = B.ntasks;
+    std::vector<int> tlev((size_t)B.ntasks);
+    for (int l = 0; l < L.nlev; ++l)
+        for (int t = B.h_task_ptr[l]; t < B.h_task_ptr[l + 1]; ++t) tlev[t] = l;
     JV_TRY(halloc_n(h, &B.rows, n));
     JV_TRY(halloc_n(h, &B.task_lo, B.ntasks));
     JV_TRY(halloc_n(h, &B.task_hi, B.ntasks));
+    JV_TRY(halloc_n(h, &B.task_lev, B.ntasks));
+    JV_TRY(halloc_n(h, &B.task_ptr, L.nlev + 1));
+    JV_CUDA(cudaMemcpyAsync(B.task_lev, tlev.data(), tlev.size() * 4, cudaMemcpyHostToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(B.task_ptr, B.h_task_ptr.data(), (size_t)(L.nlev + 1) * 4,
+                            cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaMemcpyAsync(B.rows, brows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaMemcpyAsync(B.task_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaMemcpyAsync(B.task_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s));

@@ -85,6 +85,7 @@ void jv_default_options(jv_options *opt) {
     opt->fault_row = -1;
     opt->sf_ctas_per_sm = 0;
     opt->sf_backoff_ns = 0;
+    opt->sf_gate_levels = 1;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {
@@ -113,14 +114,14 @@ int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx, const jv_op
         delete h;
         return JV_ERR_CUDA;
     }
-    if (cudaMalloc(&h->ticket, 4 * sizeof(unsigned)) != cudaSuccess ||
+    if (cudaMalloc(&h->ticket, 8 * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&h->status, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->h_status, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         destroy_handle(h);
         return JV_ERR_NOMEM;
     }
-    if (cudaMemsetAsync(h->ticket, 0, 4 * sizeof(unsigned), h->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(h->ticket, 0, 8 * sizeof(unsigned), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->status, 0xff, 8, h->stream) != cudaSuccess) {
         destroy_handle(h);
         return JV_ERR_CUDA;

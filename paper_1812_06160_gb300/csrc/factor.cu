@@ -48,6 +48,8 @@ struct FactorArgs {
     const int *rowptr, *diag, *kdiag, *pair_ptr;
     const int2 *pairs;
     const int *rows, *task_lo, *task_hi;
+    const int *task_lev, *task_ptr;   // level gate (SYNCFREE)
+    int gate_levels;
     int task_begin, task_end;     // LEVEL: this level's tasks; SYNCFREE: all tasks
     const void *vals;             // A's values (TV)
     void *lu;                     // factor (TL); sentinel-filled in SYNCFREE mode
@@ -72,7 +74,8 @@ template <> struct RN<float> {
 // Bounded spin until the U value at p is published; `u` is a first read.
 template <class T>
 __device__ __forceinline__ typename Bits<T>::U settle(const T *p, typename Bits<T>::U u,
-                                                      const FactorArgs &a, int r) {
+                                                      const FactorArgs &a, int r,
+                                                      bool &fail) {
     using B = Bits<T>;
     using U = typename B::U;
     if (u != B::kSent) return u;
@@ -84,12 +87,13 @@ __device__ __forceinline__ typename Bits<T>::U settle(const T *p, typename Bits<
         if (u != B::kSent) return u;
         if ((++it & 15u) == 0) {
             if (sf_aborted(a.ticket)) {           // another wait gave up: so does this row
-                report(a.status, JV_ERR_TIMEOUT, r);
+                fail = true;                      // (silently: that wait has reported)
                 return B::kCanonNan;
             }
             if (clock64() - t0 > a.timeout) {
                 report(a.status, JV_ERR_TIMEOUT, r);
                 sf_abort(a.ticket);
+                fail = true;
                 return B::kCanonNan;
             }
         }
@@ -117,7 +121,7 @@ __device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, T d) {
 
 // ------------------------------------------------------- one lane per row
 template <class TV, class TL, bool SF>
-__device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi,
+__device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi, unsigned gate,
                                              unsigned char *smem) {
     using B = Bits<TL>;
     using U = typename B::U;
@@ -160,6 +164,24 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             if (e < np) { OPOS(nl + e) = pr[e].y; TGT(e) = (unsigned char)(pr[e].x - rs); }
         }
     }
+    if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
+    // factor the row from its operands in shared memory and publish it
+    auto finish = [&]() {
+        int j = 0;
+        for (int p = 0; p < nl; ++p) {
+            const TL lik = RN<TL>::div(V(p), V(len + p));
+            for (const int j1 = STEP_END(p); j < j1; ++j) {
+                const int t = TGT(j);
+                V(t) = RN<TL>::fms(lik, V(len + nl + j), V(t));
+            }
+            V(p) = lik;
+        }
+        pivot_check<TL>(a, r, V(nl));
+        for (int e = 0; e < len; ++e) {
+            if (!SF || e < nl) lu[rs + e] = V(e);
+            else if (r != a.fault_row) publish<TL>(lu + rs + e, V(e));
+        }
+    };
     long long t0 = 0;
     unsigned rounds = 0;
     int wb = 0, wend = 0;
@@ -187,25 +209,14 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             }
         }
         if (got == m) {
-            int j = 0;
-            for (int p = 0; p < nl; ++p) {
-                const TL lik = RN<TL>::div(V(p), V(len + p));
-                for (const int j1 = STEP_END(p); j < j1; ++j) {
-                    const int t = TGT(j);
-                    V(t) = RN<TL>::fms(lik, V(len + nl + j), V(t));
-                }
-                V(p) = lik;
-            }
-            pivot_check<TL>(a, r, V(nl));
-            for (int e = 0; e < len; ++e) {
-                if (!SF || e < nl) lu[rs + e] = V(e);
-                else if (r != a.fault_row) publish<TL>(lu + rs + e, V(e));
-            }
+            finish();
             done = true;
         } else if (SF && got < wend) {
             if (rounds++ == 0) t0 = clock64();
             if ((rounds & 15u) == 0) {
-                if (sf_aborted(a.ticket) || clock64() - t0 > a.timeout) {
+                if (sf_aborted(a.ticket)) {
+                    done = true;                  // another wait gave up and reported
+                } else if (clock64() - t0 > a.timeout) {
                     report(a.status, JV_ERR_TIMEOUT, r);
                     sf_abort(a.ticket);
                     done = true;
@@ -217,7 +228,8 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 
 // ------------------------------------------------------- one warp per row
 template <class TV, class TL, bool SF>
-__device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsigned char *smem) {
+__device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsigned gate,
+                                            unsigned char *smem) {
     using B = Bits<TL>;
     using U = typename B::U;
     const int lane = threadIdx.x & 31;
@@ -227,6 +239,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     const int j0 = __ldg(a.pair_ptr + rs);
     const int np = __ldg(a.pair_ptr + rd) - j0;
     const int m = nl + np;
+    bool fail = false;                 // a wait gave up: publish nothing
     TL *lu = static_cast<TL *>(a.lu);
     const TV *vals = static_cast<const TV *>(a.vals);
     const size_t need = (size_t)(len + m) * sizeof(TL) + (size_t)(np + nl) * sizeof(int);
@@ -236,6 +249,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     int *tgt = reinterpret_cast<int *>(uv + m);                // fast path only
     int *send = tgt + np;
     for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
+    if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
     if (fast) {
         for (int e = lane; e < np; e += kWarp) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
         for (int e = lane; e < nl; e += kWarp) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
@@ -254,7 +268,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k)
                 if (src[k] >= 0) {
-                    if (SF) u[k] = settle<TL>(lu + src[k], u[k], a, r);
+                    if (SF) u[k] = settle<TL>(lu + src[k], u[k], a, r, fail);
                     uv[e0 + k * kWarp + lane] = B::from(u[k]);
                 }
         }
@@ -267,7 +281,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
             ukk = uv[p];
         } else {
             const TL *src = lu + __ldg(a.kdiag + rs + p);
-            ukk = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r) : first_read<TL, SF>(src));
+            ukk = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
         }
         const TL lik = RN<TL>::div(w[p], ukk);
         const int je = fast ? send[p] : __ldg(a.pair_ptr + rs + p + 1) - j0;
@@ -281,7 +295,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
                 const int2 tq = __ldg(a.pairs + j0 + j);
                 t = tq.x - rs;
                 const TL *src = lu + tq.y;
-                uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r) : first_read<TL, SF>(src));
+                uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
             }
             w[t] = RN<TL>::fms(lik, uq, w[t]);
         }
@@ -290,6 +304,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         if (lane == 0) w[p] = lik;
     }
     __syncwarp();
+    if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) pivot_check<TL>(a, r, w[nl]);
     for (int e = lane; e < len; e += kWarp) {
         const TL v = w[e];
@@ -302,8 +317,9 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
 template <class TV, class TL, bool SF>
 __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
-    if (hi & kLongBit) factor_warp<TV, TL, SF>(a, lo, smem);
-    else factor_lanes<TV, TL, SF>(a, lo, hi, smem);
+    const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, task) : 0u;
+    if (hi & kLongBit) factor_warp<TV, TL, SF>(a, lo, gate, smem);
+    else factor_lanes<TV, TL, SF>(a, lo, hi, gate, smem);
     __syncwarp();
 }
 
@@ -381,6 +397,9 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.rows = W.rows;
     a.task_lo = W.task_lo;
     a.task_hi = W.task_hi;
+    a.task_lev = W.task_lev;
+    a.task_ptr = W.task_ptr;
+    a.gate_levels = h->opt.sf_gate_levels;
     a.vals = vals;
     a.lu = lu;
     a.scratch = h->fscratch;

@@ -148,6 +148,7 @@ __device__ __forceinline__ void sf_for_each_task(unsigned *ticket, int ntasks, F
         if (lane == 0) next = atomicAdd(ticket, 1u);
         run(task);
         __syncwarp();
+        if (lane == 0) atomicAdd(ticket + 3, 1u);        // finished tasks (level gate)
         task = __shfl_sync(0xffffffffu, (int)next, 0);
     }
 }
@@ -161,6 +162,7 @@ __device__ __forceinline__ void sf_finish(unsigned *ticket) {
             atomicExch(ticket, 0u);
             atomicExch(ticket + 1, 0u);
             atomicExch(ticket + 2, 0u);
+            atomicExch(ticket + 3, 0u);
         }
     }
 }
@@ -168,6 +170,39 @@ __device__ __forceinline__ bool sf_aborted(const unsigned *ticket) {
     return ld_relaxed(ticket + 2) != 0u;
 }
 __device__ __forceinline__ void sf_abort(unsigned *ticket) { atomicExch(ticket + 2, 1u); }
+
+// Level gate.  Word [3] counts finished tasks.  A task whose operands lie
+// in levels far below the dependency front would poll them for many rounds
+// and, with thousands of such rows in flight, the polls crowd each SM's load
+// path and slow the rows that are about to become ready.  So a task first
+// sleeps until `gate` tasks have finished (the tasks of the levels more
+// than gate-levels below its own), with a pause that shrinks as the count
+// approaches the gate, and only then polls its operands.  The count is a
+// hint, never a correctness condition (every operand is still awaited on its
+// own word); it reaches the gate because the tasks below it wait on nothing
+// above.  Bounded by the wait bound, after which the task simply polls.
+// Warp-uniform.
+__device__ __forceinline__ unsigned sf_gate_of(const int *task_lev, const int *task_ptr,
+                                               int gate_levels, int task) {
+    if (gate_levels <= 0) return 0u;
+    const int l = __ldg(task_lev + task) - gate_levels;
+    return l > 0 ? (unsigned)__ldg(task_ptr + l) : 0u;
+}
+__device__ __forceinline__ void sf_gate_wait(unsigned *ticket, unsigned gate, long long timeout) {
+    unsigned c = ld_relaxed(ticket + 3);
+    if (c >= gate) return;
+    const long long t0 = clock64();
+    for (unsigned it = 1;; ++it) {
+        const unsigned gap = gate - c;
+        __nanosleep(gap > 1024u ? 2048u : (gap < 16u ? 32u : 2u * gap));
+        c = ld_relaxed(ticket + 3);
+        if (c >= gate) return;
+        // past the wait bound (or after an abort) stop sleeping and poll: the
+        // gate is only a hint, the operand waits that follow are the ones
+        // that detect and report a missing row
+        if ((it & 7u) == 0 && (sf_aborted(ticket) || clock64() - t0 > timeout)) return;
+    }
+}
 
 // ---------------------------------------------------------------- sentinels
 // In sync-free solves the output vector itself carries readiness: it is
@@ -231,6 +266,8 @@ struct Bins {
     int *rows = nullptr;       // [n] binned rows
     int *task_lo = nullptr;    // [ntasks] first position in rows
     int *task_hi = nullptr;    // [ntasks] end position, | kLongBit for a long-row task
+    int *task_lev = nullptr;   // [ntasks] level of every task
+    int *task_ptr = nullptr;   // [nlev+1] first task of every level (device copy)
     int ntasks = 0;
     int nlong = 0;
     std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
@@ -297,7 +334,8 @@ struct jv_handle_s {
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;
     // scratch shared by the sync-free kernels
-    unsigned *ticket = nullptr;              // [4]: next CTA ticket, finished CTAs, abort
+    unsigned *ticket = nullptr;              // [8]: next task ticket, finished CTAs, abort,
+                                             // finished tasks
     unsigned long long *status = nullptr;    // device status word
     unsigned long long *h_status = nullptr;  // pinned host mirror
     int bad_row = -1;                        // row of the last analysis error

@@ -62,7 +62,8 @@ template <> struct RN<float> {
 // Spin (bounded) until *p no longer holds the sentinel; `u` is a first read.
 template <class TX>
 __device__ __forceinline__ typename Bits<TX>::U settle(const TX *p, typename Bits<TX>::U u,
-                                                       const TriArgs &a, int r) {
+                                                       const TriArgs &a, int r,
+                                                       bool &fail) {
     using B = Bits<TX>;
     using U = typename B::U;
     if (u != B::kSent) return u;
@@ -74,12 +75,13 @@ __device__ __forceinline__ typename Bits<TX>::U settle(const TX *p, typename Bit
         if (u != B::kSent) return u;
         if ((++it & 15u) == 0) {
             if (sf_aborted(a.ticket)) {           // another wait gave up: so does this row
-                report(a.status, JV_ERR_TIMEOUT, r);
+                fail = true;                      // (silently: that wait has reported)
                 return B::kCanonNan;
             }
             if (clock64() - t0 > a.timeout) {
                 report(a.status, JV_ERR_TIMEOUT, r);
                 sf_abort(a.ticket);
+                fail = true;
                 return B::kCanonNan;
             }
         }
@@ -136,6 +138,16 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         len = a.end.at(r) - qb;
         s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
         if (!a.unit) d = __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+        if (len > 0) {               // first window: indices and values
+            wend = min(kPoll, len);
+#pragma unroll
+            for (int k = 0; k < kPoll; ++k)
+                if (k < wend) {
+                    const int q = a.reverse ? qb + len - 1 - k : qb + k;
+                    jw[k] = __ldg(a.idx + q);
+                    vw[k] = load_val<TL>(a, q);
+                }
+        }
     }
     U u[kPoll];
     long long t0 = 0;
@@ -187,7 +199,9 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         if (SF && !done && !progress) {
             if (rounds++ == 0) t0 = clock64();
             if ((rounds & 15u) == 0) {
-                if (sf_aborted(a.ticket) || clock64() - t0 > a.timeout) {
+                if (sf_aborted(a.ticket)) {
+                    done = true;                  // another wait gave up and reported
+                } else if (clock64() - t0 > a.timeout) {
                     report(a.status, JV_ERR_TIMEOUT, r);
                     sf_abort(a.ticket);
                     done = true;
@@ -210,6 +224,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     const int len = a.end.at(r) - qb;
     TL s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
     const TL d = a.unit ? (TL)1 : __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    bool fail = false;                 // a wait gave up: publish nothing
     for (int c0 = 0; c0 < len; c0 += CH) {
         int q[kUnroll];
         TL v[kUnroll];
@@ -229,7 +244,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
         for (int k = 0; k < kUnroll; ++k) {
             xv[k] = 0;
             if (q[k] >= 0) {
-                if (SF) u[k] = settle<TX>(x + __ldg(a.idx + q[k]), u[k], a, r);
+                if (SF) u[k] = settle<TX>(x + __ldg(a.idx + q[k]), u[k], a, r, fail);
                 xv[k] = (TL)B::from(u[k]);
             } else {
                 v[k] = 0;
@@ -244,6 +259,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
                 if (c0 + k * kWarp + l < len) s = RN<TL>::fms(vl, xl, s);
             }
     }
+    if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
 }
 
@@ -282,6 +298,7 @@ __device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
         const int c = c0 + lane;
         const bool ok = c < a.nrhs;
         TL s = ok ? (TL)b[(size_t)r * ld + c] : (TL)0;
+        bool fail = false;             // a wait gave up: publish nothing
         for (int e0 = 0; e0 < len; e0 += kUnroll) {
             int j[kUnroll];
             TL v[kUnroll];
@@ -301,13 +318,13 @@ __device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
 #pragma unroll
                 for (int k = 0; k < kUnroll; ++k) {
                     if (j[k] >= 0) {
-                        if (SF) u[k] = settle<TX>(x + (size_t)j[k] * ld + c, u[k], a, r);
+                        if (SF) u[k] = settle<TX>(x + (size_t)j[k] * ld + c, u[k], a, r, fail);
                         s = RN<TL>::fms(v[k], (TL)B::from(u[k]), s);
                     }
                 }
             }
         }
-        if (ok) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, a.unit ? s : RN<TL>::div(s, d));
+        if (ok && !fail) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, a.unit ? s : RN<TL>::div(s, d));
     }
 }
 
