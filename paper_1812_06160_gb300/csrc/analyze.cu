@@ -278,7 +278,9 @@ __global__ void k_row_costs(int n, const int *rowptr, const int *diag, const int
 }
 
 // Host-side binning of one level structure (see Bins).
-int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, Bins &B) {
+// ops[r]: operands a one-lane row r awaits (sets the poll window).
+int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, const int *ops,
+              Bins &B) {
     const int n = h->n;
     cudaStream_t s = h->stream;
     std::vector<int> rows((size_t)n), brows, lo, hi;
@@ -308,6 +310,11 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, Bi
     }
     B.ntasks = (int)lo.size();
     B.h_task_ptr[L.nlev] = B.ntasks;
+    int most = 0;
+    for (int t = 0; t < B.ntasks; ++t)
+        if (!(hi[t] & kLongBit))
+            for (int p = lo[t]; p < hi[t]; ++p) most = std::max(most, ops[brows[p]]);
+    B.window = most <= 2 ? 2 : most <= 4 ? 4 : kPoll;
     std::vector<int> tlev((size_t)B.ntasks);
     for (int l = 0; l < L.nlev; ++l)
         for (int t = B.h_task_ptr[l]; t < B.h_task_ptr[l + 1]; ++t) tlev[t] = l;
@@ -444,8 +451,12 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     JV_CUDA(cudaStreamSynchronize(s));
     const int long_deps = h->opt.long_row > 0 ? h->opt.long_row : kLongDeps;
     for (int k = 0; k < 4; ++k)
-        JV_TRY(make_bins(h, h->ls[k], cost.data() + (size_t)k * n, long_deps, h->ls[k].bins));
-    JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, kLaneSlot, h->fbins));
+        JV_TRY(make_bins(h, h->ls[k], cost.data() + (size_t)k * n, long_deps,
+                         cost.data() + (size_t)k * n, h->ls[k].bins));
+    std::vector<int> fops((size_t)n);          // factor operands: cost minus the row's length
+    for (int i = 0; i < n; ++i) fops[i] = cost[4 * (size_t)n + i] - (hrp[i + 1] - hrp[i]);
+    JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, kLaneSlot, fops.data(),
+                     h->fbins));
     return plan_bands(h);
 }
 

@@ -20,7 +20,7 @@
 //
 // Work list (see Bins): a short task holds up to 32 rows of one level, one
 // lane per row (a per-lane slot interleaved across the warp's shared memory);
-// every lane polls its next kPoll operands, keeps the ready prefix, and
+// every lane polls its next W operands (4 or 8), keeps the ready prefix, and
 // factors and publishes its row as soon as the last one arrives -- no lane
 // waits for another's dependencies.  A long task is one row run by the whole
 // warp (operands prefetched, pairs split over the lanes, steps in order);
@@ -120,7 +120,7 @@ __device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, T d) {
 }
 
 // ------------------------------------------------------- one lane per row
-template <class TV, class TL, bool SF>
+template <class TV, class TL, bool SF, int W>
 __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi, unsigned gate,
                                              unsigned char *smem) {
     using B = Bits<TL>;
@@ -163,6 +163,13 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             if (e < nl) { OPOS(e) = kd[e]; STEP_END(e) = (unsigned char)(se[e] - j0); }
             if (e < np) { OPOS(nl + e) = pr[e].y; TGT(e) = (unsigned char)(pr[e].x - rs); }
         }
+        if (SF && gate) {               // bring the operands' lines into L2 before sleeping
+#pragma unroll
+            for (int e = 0; e < kLaneSlot; ++e) {
+                if (e < nl) prefetch_l2(lu + kd[e]);
+                if (e < np) prefetch_l2(lu + pr[e].y);
+            }
+        }
     }
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
     // factor the row from its operands in shared memory and publish it
@@ -185,21 +192,21 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     long long t0 = 0;
     unsigned rounds = 0;
     int wb = 0, wend = 0;
-    U u[kPoll];
+    U u[W];
     while (__any_sync(0xffffffffu, !done)) {
         if (done) continue;
         if (got == wend) {              // next window of operands [wb, wend)
             wb = got;
-            wend = min(got + kPoll, m);
+            wend = min(got + W, m);
         }
         // (re-)read every operand of the window not taken yet; they tend to be
         // published together, so they are all polled in the same round
 #pragma unroll
-        for (int k = 0; k < kPoll; ++k)
+        for (int k = 0; k < W; ++k)
             if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(lu + OPOS(wb + k));
         bool ok = true;
 #pragma unroll
-        for (int k = 0; k < kPoll; ++k) {
+        for (int k = 0; k < W; ++k) {
             if (wb + k < got) continue;
             if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
                 V(len + wb + k) = B::from(u[k]);
@@ -314,27 +321,27 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     __syncwarp();                                              // shared memory reusable
 }
 
-template <class TV, class TL, bool SF>
+template <class TV, class TL, bool SF, int W>
 __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
     const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, task) : 0u;
     if (hi & kLongBit) factor_warp<TV, TL, SF>(a, lo, gate, smem);
-    else factor_lanes<TV, TL, SF>(a, lo, hi, gate, smem);
+    else factor_lanes<TV, TL, SF, W>(a, lo, hi, gate, smem);
     __syncwarp();
 }
 
-template <class TV, class TL, bool SF>
+template <class TV, class TL, bool SF, int W>
 __global__ void __launch_bounds__(kBlock, 1) k_ilu0(FactorArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int wib = threadIdx.x >> 5;
     unsigned char *smem = dyn_smem + (size_t)wib * kWarpSmem;
     if (SF) {
         sf_for_each_task(a.ticket, a.task_end,
-                         [&](int task) { factor_task<TV, TL, SF>(a, task, smem); });
+                         [&](int task) { factor_task<TV, TL, SF, W>(a, task, smem); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-        if (task < a.task_end) factor_task<TV, TL, SF>(a, task, smem);
+        if (task < a.task_end) factor_task<TV, TL, SF, W>(a, task, smem);
     }
 }
 
@@ -360,14 +367,18 @@ int ensure_scratch(jv_handle h) {
     return JV_OK;
 }
 
-template <class TV, class TL, bool SF>
-int launch(int grid, cudaStream_t s, const FactorArgs &a) {
-    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <class TV, class TL, bool SF, int W>
+int launch_w(int grid, cudaStream_t s, const FactorArgs &a) {
+    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kBlockSmem));
     count_launch();
-    k_ilu0<TV, TL, SF><<<grid, kBlock, kBlockSmem, s>>>(a);
+    k_ilu0<TV, TL, SF, W><<<grid, kBlock, kBlockSmem, s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
+}
+template <class TV, class TL, bool SF>
+int launch(int window, int grid, cudaStream_t s, const FactorArgs &a) {
+    return window <= 4 ? launch_w<TV, TL, SF, 4>(grid, s, a) : launch_w<TV, TL, SF, kPoll>(grid, s, a);
 }
 
 template <class TV, class TL>
@@ -413,12 +424,13 @@ int run(jv_handle h, const void *vals, void *lu) {
         if (rc) return rc;
         a.task_begin = 0;
         a.task_end = W.ntasks;
-        return launch<TV, TL, true>(sf_grid(h, W.ntasks), s, a);
+        return launch<TV, TL, true>(W.window, sf_grid(h, W.ntasks), s, a);
     }
     for (int l = 0; l < L.nlev; ++l) {
         a.task_begin = W.h_task_ptr[l];
         a.task_end = W.h_task_ptr[l + 1];
-        int rc = launch<TV, TL, false>(grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+        int rc = launch<TV, TL, false>(W.window, grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s,
+                                       a);
         if (rc) return rc;
     }
     return JV_OK;

@@ -17,7 +17,7 @@ constexpr int kBlock = 256;              // threads per CTA for every kernel her
 constexpr int kWarpsPerBlock = kBlock / kWarp;
 constexpr long long kDefaultSpin = 1ll << 32;
 constexpr int kUnroll = 4;        // entries per lane per step (cooperative kernels)
-constexpr int kPoll = 8;          // operands polled per lane per round (one-lane-per-row kernels)
+constexpr int kPoll = 8;          // largest poll window of the one-lane-per-row kernels
 constexpr int kLongDeps = 24;     // solve rows with more dependencies run one per warp
 constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
 constexpr int kSpmvRows = 256;    // rows per spmv block (one summing thread each)
@@ -95,6 +95,11 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Hint: bring the line holding p into L2 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // ------------------------------------------------------ sync-free launches
@@ -270,6 +275,8 @@ struct Bins {
     int *task_ptr = nullptr;   // [nlev+1] first task of every level (device copy)
     int ntasks = 0;
     int nlong = 0;
+    int window = 8;            // operands a one-lane row polls per round: 2, 4 or 8, the
+                               // smallest holding the most operands of any short row
     std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
 };
 

@@ -12,7 +12,10 @@
 // loads run in parallel.
 //
 // Work list (see Bins): a short task holds up to 32 rows of one level, one
-// lane per row.  Every lane polls the next kPoll dependencies of its own row,
+// lane per row.  Every lane polls the next W dependencies of its own row (a
+// window of 2, 4 or 8, the smallest that holds the longest such row: every
+// slot is an unrolled step of the poll loop, and its instructions are on the
+// critical path of every level),
 // consumes the ready prefix in order and publishes its row the moment the
 // last one arrives, so no lane waits for another lane's dependencies.  A
 // long task is one row with many dependencies; the whole warp loads 32 x
@@ -118,9 +121,9 @@ __device__ __forceinline__ void store_x(const TriArgs &a, bool sf, TX *p, int r,
 }
 
 // Short task: rows[lo..hi) of one level, one lane per row, polled independently.
-// The indices and values of the next kPoll dependencies (a window) are loaded
+// The indices and values of the next W dependencies (a window) are loaded
 // once; every poll round then re-reads only the x words still missing.
-template <class TL, class TB, class TX, bool SF>
+template <class TL, class TB, class TX, bool SF, int W>
 __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     using B = Bits<TX>;
     using U = typename B::U;
@@ -130,8 +133,8 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     bool done = pos >= hi;
     int r = 0, qb = 0, len = 0, e = 0, wb = 0, wend = 0;
     TL s = 0, d = 1;
-    int jw[kPoll];
-    TL vw[kPoll];
+    int jw[W];
+    TL vw[W];
     if (!done) {
         r = __ldg(a.rows + pos);
         qb = a.beg.at(r);
@@ -139,9 +142,9 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
         if (!a.unit) d = __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
         if (len > 0) {               // first window: indices and values
-            wend = min(kPoll, len);
+            wend = min(W, len);
 #pragma unroll
-            for (int k = 0; k < kPoll; ++k)
+            for (int k = 0; k < W; ++k)
                 if (k < wend) {
                     const int q = a.reverse ? qb + len - 1 - k : qb + k;
                     jw[k] = __ldg(a.idx + q);
@@ -149,7 +152,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                 }
         }
     }
-    U u[kPoll];
+    U u[W];
     long long t0 = 0;
     unsigned rounds = 0;
     // The loop body is warp-uniform (finished lanes only mask their work),
@@ -160,9 +163,9 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         if (!done && e == wend && e < len) {
             // next window [wb, wend): indices, values and a first read of every x
             wb = e;
-            wend = min(e + kPoll, len);
+            wend = min(e + W, len);
 #pragma unroll
-            for (int k = 0; k < kPoll; ++k)
+            for (int k = 0; k < W; ++k)
                 if (wb + k < wend) {
                     const int q = a.reverse ? qb + len - 1 - (wb + k) : qb + wb + k;
                     jw[k] = __ldg(a.idx + q);
@@ -173,7 +176,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         // tend to arrive together, so they are all polled in the same round
         bool progress = !done && e == len;
 #pragma unroll
-        for (int k = 0; k < kPoll; ++k)
+        for (int k = 0; k < W; ++k)
             if (!done && wb + k >= e && wb + k < wend) {
                 u[k] = first_read<TX, SF>(x + jw[k]);
                 if (wb + k == e) progress = !SF || u[k] != B::kSent;
@@ -182,7 +185,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
             // consume the ready prefix, in order
             bool ok = true;
 #pragma unroll
-            for (int k = 0; k < kPoll; ++k) {
+            for (int k = 0; k < W; ++k) {
                 if (wb + k < e) continue;
                 if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
                     s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
@@ -263,22 +266,23 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
 }
 
-template <class TL, class TB, class TX, bool SF>
+template <class TL, class TB, class TX, bool SF, int W>
 __device__ __forceinline__ void trsv_task(const TriArgs &a, int task) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
     if (hi & kLongBit) trsv_warp<TL, TB, TX, SF>(a, lo);
-    else trsv_lanes<TL, TB, TX, SF>(a, lo, hi);
+    else trsv_lanes<TL, TB, TX, SF, W>(a, lo, hi);
 }
 
-template <class TL, class TB, class TX, bool SF>
+template <class TL, class TB, class TX, bool SF, int W>
 __global__ void __launch_bounds__(kBlock) k_trsv(TriArgs a) {
     const int wib = threadIdx.x >> 5;
     if (SF) {
-        sf_for_each_task(a.ticket, a.task_end, [&](int task) { trsv_task<TL, TB, TX, SF>(a, task); });
+        sf_for_each_task(a.ticket, a.task_end,
+                         [&](int task) { trsv_task<TL, TB, TX, SF, W>(a, task); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-        if (task < a.task_end) trsv_task<TL, TB, TX, SF>(a, task);
+        if (task < a.task_end) trsv_task<TL, TB, TX, SF, W>(a, task);
     }
 }
 
@@ -341,10 +345,12 @@ __global__ void __launch_bounds__(kBlock) k_trsm(TriArgs a) {
 }
 
 template <class TL, class TB, class TX, bool SF>
-int launch(bool multi, int grid, cudaStream_t s, const TriArgs &a) {
+int launch(bool multi, int window, int grid, cudaStream_t s, const TriArgs &a) {
     count_launch();
     if (multi) k_trsm<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
-    else k_trsv<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= 2) k_trsv<TL, TB, TX, SF, 2><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= 4) k_trsv<TL, TB, TX, SF, 4><<<grid, kBlock, 0, s>>>(a);
+    else k_trsv<TL, TB, TX, SF, 8><<<grid, kBlock, 0, s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }
@@ -392,13 +398,13 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
         if (rc) return rc;
         a.task_begin = 0;
         a.task_end = multi ? h->n : W.ntasks;
-        return launch<TL, TB, TX, true>(multi, sf_grid(h, a.task_end), s, a);
+        return launch<TL, TB, TX, true>(multi, W.window, sf_grid(h, a.task_end), s, a);
     }
     for (int l = 0; l < L.nlev; ++l) {
         a.task_begin = multi ? L.h_ptr[l] : W.h_task_ptr[l];
         a.task_end = multi ? L.h_ptr[l + 1] : W.h_task_ptr[l + 1];
-        int rc = launch<TL, TB, TX, false>(multi, grid_for(a.task_end - a.task_begin, kWarpsPerBlock),
-                                           s, a);
+        int rc = launch<TL, TB, TX, false>(multi, W.window,
+                                           grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
         if (rc) return rc;
     }
     return JV_OK;
