@@ -191,8 +191,8 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     };
     long long t0 = 0;
     unsigned rounds = 0;
-    int wb = 0, wend = 0;
     U u[W];
+    int wb = 0, wend = 0;
     while (__any_sync(0xffffffffu, !done)) {
         if (done) continue;
         if (got == wend) {              // next window of operands [wb, wend)

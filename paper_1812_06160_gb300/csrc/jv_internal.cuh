@@ -276,7 +276,8 @@ struct Bins {
     int ntasks = 0;
     int nlong = 0;
     int window = 8;            // operands a one-lane row polls per round: 2, 4 or 8, the
-                               // smallest holding the most operands of any short row
+                               // smallest holding the most operands of any short row;
+                               // 9 = more than 8 (rows span several windows of 8)
     std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
 };
 

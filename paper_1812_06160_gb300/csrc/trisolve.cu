@@ -123,7 +123,7 @@ __device__ __forceinline__ void store_x(const TriArgs &a, bool sf, TX *p, int r,
 // Short task: rows[lo..hi) of one level, one lane per row, polled independently.
 // The indices and values of the next W dependencies (a window) are loaded
 // once; every poll round then re-reads only the x words still missing.
-template <class TL, class TB, class TX, bool SF, int W>
+template <class TL, class TB, class TX, bool SF, int W, bool ONE>
 __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     using B = Bits<TX>;
     using U = typename B::U;
@@ -155,6 +155,40 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     U u[W];
     long long t0 = 0;
     unsigned rounds = 0;
+    if constexpr (SF && ONE) {
+        // Every row of the work list fits one window (len <= W): each round
+        // polls only the words not seen yet, and a row finishes -- its
+        // ordered chain, then its store -- in the round its last word arrives.
+        unsigned seen = 0u;
+        const unsigned need = (1u << len) - 1u;
+        while (__any_sync(0xffffffffu, !done)) {
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (!done && k < len && !((seen >> k) & 1u)) u[k] = ld_relaxed(reinterpret_cast<const U *>(x + jw[k]));
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (!done && k < len && !((seen >> k) & 1u) && u[k] != B::kSent) seen |= 1u << k;
+            if (!done && seen == need) {
+#pragma unroll
+                for (int k = 0; k < W; ++k)
+                    if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+                done = true;
+            } else if (!done) {
+                if (rounds++ == 0) t0 = clock64();
+                if ((rounds & 15u) == 0) {
+                    if (sf_aborted(a.ticket)) {
+                        done = true;                  // another wait gave up and reported
+                    } else if (clock64() - t0 > a.timeout) {
+                        report(a.status, JV_ERR_TIMEOUT, r);
+                        sf_abort(a.ticket);
+                        done = true;
+                    }
+                }
+            }
+        }
+        return;
+    }
     // The loop body is warp-uniform (finished lanes only mask their work),
     // so the consume step -- FP64 fused multiply-adds, slow on this part's
     // narrow FP64 pipe even when predicated off -- is skipped outright in
@@ -266,23 +300,23 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
 }
 
-template <class TL, class TB, class TX, bool SF, int W>
+template <class TL, class TB, class TX, bool SF, int W, bool ONE>
 __device__ __forceinline__ void trsv_task(const TriArgs &a, int task) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
     if (hi & kLongBit) trsv_warp<TL, TB, TX, SF>(a, lo);
-    else trsv_lanes<TL, TB, TX, SF, W>(a, lo, hi);
+    else trsv_lanes<TL, TB, TX, SF, W, ONE>(a, lo, hi);
 }
 
-template <class TL, class TB, class TX, bool SF, int W>
-__global__ void __launch_bounds__(kBlock) k_trsv(TriArgs a) {
+template <class TL, class TB, class TX, bool SF, int W, bool ONE>
+__global__ void __launch_bounds__(kBlock, 1) k_trsv(TriArgs a) {
     const int wib = threadIdx.x >> 5;
     if (SF) {
         sf_for_each_task(a.ticket, a.task_end,
-                         [&](int task) { trsv_task<TL, TB, TX, SF, W>(a, task); });
+                         [&](int task) { trsv_task<TL, TB, TX, SF, W, ONE>(a, task); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-        if (task < a.task_end) trsv_task<TL, TB, TX, SF, W>(a, task);
+        if (task < a.task_end) trsv_task<TL, TB, TX, SF, W, ONE>(a, task);
     }
 }
 
@@ -348,9 +382,10 @@ template <class TL, class TB, class TX, bool SF>
 int launch(bool multi, int window, int grid, cudaStream_t s, const TriArgs &a) {
     count_launch();
     if (multi) k_trsm<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
-    else if (window <= 2) k_trsv<TL, TB, TX, SF, 2><<<grid, kBlock, 0, s>>>(a);
-    else if (window <= 4) k_trsv<TL, TB, TX, SF, 4><<<grid, kBlock, 0, s>>>(a);
-    else k_trsv<TL, TB, TX, SF, 8><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= 2) k_trsv<TL, TB, TX, SF, 2, true><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= 4) k_trsv<TL, TB, TX, SF, 4, true><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= kPoll) k_trsv<TL, TB, TX, SF, kPoll, true><<<grid, kBlock, 0, s>>>(a);
+    else k_trsv<TL, TB, TX, SF, kPoll, false><<<grid, kBlock, 0, s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }
