@@ -464,6 +464,32 @@ def main(argv=None):
                          "true_relres": kinfo["true_relres"], "converged": kinfo["converged"]}
         line["krylov_time_to_1e-8"] = {"method": "pcg" if pcg else "fgmres(30)", **kry}
 
+    if not meta["adjoint"]:
+        # FP32 factor and solves against the FP64 path (itself bit-exact with
+        # the FP64 oracle in the tests): largest entrywise relative error over
+        # entries above 1e-6 of the largest magnitude, and the normwise error
+        import torch as _t
+        vals64 = torch.tensor(c["vals"], device=dev)
+        b64 = torch.tensor(c["b"], device=dev)
+        if a.reorder:
+            vals64 = jv.jv_permute_values(h, vals64)
+            b64 = jv.jv_permute_vector(h, b64)
+
+        def rel(x32, x64):
+            x32 = x32.to(_t.float64)
+            big = x64.abs() > 1e-6 * x64.abs().max()
+            ent = ((x32 - x64).abs()[big] / x64.abs()[big]).max().item()
+            return {"max_entry_rel": ent,
+                    "normwise_rel": ((x32 - x64).abs().max() / x64.abs().max()).item()}
+        l64 = jv.jv_ilu0_factor(h, vals64)
+        l32 = jv.jv_ilu0_factor(h, vals64, lu_dtype=_t.float32)
+        y64 = jv.jv_lsolve(h, l64, b64)
+        y32 = jv.jv_lsolve(h, l32, b64.float())
+        z64 = jv.jv_usolve(h, l64, y64)
+        z32 = jv.jv_usolve(h, l32, y32)
+        line["fp32_vs_fp64"] = {"factor": rel(l32, l64), "lsolve": rel(y32, y64),
+                                "usolve": rel(z32, z64)}
+
     if rank == 0 and not a.no_cpu and world == 1:
         budget = a.cpu_budget
         times = run_oracle(c, meta, a.dtype, budget)

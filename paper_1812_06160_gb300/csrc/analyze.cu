@@ -314,8 +314,8 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
     for (int t = 0; t < B.ntasks; ++t)
         if (!(hi[t] & kLongBit))
             for (int p = lo[t]; p < hi[t]; ++p) most = std::max(most, ops[brows[p]]);
-    // > kPoll: some row needs several windows (the general poll loop)
-    B.window = most <= 2 ? 2 : most <= 4 ? 4 : most <= kPoll ? kPoll : kPoll + 1;
+    // > 16: some row needs several windows of kPoll (the general poll loop)
+    B.window = most <= 2 ? 2 : most <= 4 ? 4 : most <= 8 ? 8 : most <= 16 ? 16 : 17;
     std::vector<int> tlev((size_t)B.ntasks);
     for (int l = 0; l < L.nlev; ++l)
         for (int t = B.h_task_ptr[l]; t < B.h_task_ptr[l + 1]; ++t) tlev[t] = l;

@@ -275,9 +275,9 @@ struct Bins {
     int *task_ptr = nullptr;   // [nlev+1] first task of every level (device copy)
     int ntasks = 0;
     int nlong = 0;
-    int window = 8;            // operands a one-lane row polls per round: 2, 4 or 8, the
-                               // smallest holding the most operands of any short row;
-                               // 9 = more than 8 (rows span several windows of 8)
+    int window = 8;            // operands a one-lane row polls per round: 2, 4, 8 or 16,
+                               // the smallest holding the most operands of any short
+                               // row; 17 = more (rows span several windows of kPoll)
     std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
 };
 

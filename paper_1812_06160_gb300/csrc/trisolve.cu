@@ -13,7 +13,7 @@
 //
 // Work list (see Bins): a short task holds up to 32 rows of one level, one
 // lane per row.  Every lane polls the next W dependencies of its own row (a
-// window of 2, 4 or 8, the smallest that holds the longest such row: every
+// window of 2, 4, 8 or 16, the smallest that holds the longest such row: every
 // slot is an unrolled step of the poll loop, and its instructions are on the
 // critical path of every level),
 // consumes the ready prefix in order and publishes its row the moment the
@@ -159,8 +159,13 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         // Every row of the work list fits one window (len <= W): each round
         // polls only the words not seen yet, and a row finishes -- its
         // ordered chain, then its store -- in the round its last word arrives.
+        // Wide windows (8, 16) consume the ready prefix in chunks of 4 as it
+        // grows, each chunk issued only when some lane needs it, so that only
+        // the last chunk's fused multiply-adds (64 cycles per FP64 warp
+        // instruction) follow the last arrival; narrow ones chain at the end.
         unsigned seen = 0u;
         const unsigned need = (1u << len) - 1u;
+        int e = 0;                                       // entries consumed (wide windows)
         while (__any_sync(0xffffffffu, !done)) {
 #pragma unroll
             for (int k = 0; k < W; ++k)
@@ -168,10 +173,23 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
 #pragma unroll
             for (int k = 0; k < W; ++k)
                 if (!done && k < len && !((seen >> k) & 1u) && u[k] != B::kSent) seen |= 1u << k;
-            if (!done && seen == need) {
+            if constexpr (W >= 8) {
+                const int p = done ? e : __ffs(~seen) - 1;   // ready prefix [0, p)
 #pragma unroll
-                for (int k = 0; k < W; ++k)
-                    if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                for (int q = 0; q < W; q += 4)
+                    if (__any_sync(0xffffffffu, e < q + 4 && p > q)) {
+#pragma unroll
+                        for (int k = q; k < q + 4; ++k)
+                            if (k >= e && k < p) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                    }
+                e = p;
+            }
+            if (!done && seen == need) {
+                if constexpr (W < 8) {
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+                        if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                }
                 store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
                 done = true;
             } else if (!done) {
@@ -384,7 +402,8 @@ int launch(bool multi, int window, int grid, cudaStream_t s, const TriArgs &a) {
     if (multi) k_trsm<TL, TB, TX, SF><<<grid, kBlock, 0, s>>>(a);
     else if (window <= 2) k_trsv<TL, TB, TX, SF, 2, true><<<grid, kBlock, 0, s>>>(a);
     else if (window <= 4) k_trsv<TL, TB, TX, SF, 4, true><<<grid, kBlock, 0, s>>>(a);
-    else if (window <= kPoll) k_trsv<TL, TB, TX, SF, kPoll, true><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= 8) k_trsv<TL, TB, TX, SF, 8, true><<<grid, kBlock, 0, s>>>(a);
+    else if (window <= 16) k_trsv<TL, TB, TX, SF, 16, true><<<grid, kBlock, 0, s>>>(a);
     else k_trsv<TL, TB, TX, SF, kPoll, false><<<grid, kBlock, 0, s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;

@@ -89,4 +89,8 @@ def small_matrices():
     out.append(("aniso5_41", rp, ci, v))
     rp, ci, v = W.powerlaw(6000, kmax=400, seed_pattern=11, seed_values=12)
     out.append(("powerlaw6000", rp, ci, v))
+    # 20 dependencies per row: one-lane rows that span several poll windows
+    rp, ci, v = W.stencil((800, 1, 1), [(-d, 0, 0) for d in range(20, 0, -1)] +
+                          [(d, 0, 0) for d in range(1, 21)], [-0.02] * 40, 1.0)
+    out.append(("band20_800", rp, ci, v))
     return out
