@@ -62,6 +62,8 @@ def _load():
             "jvo_permute": [_I, _P, _P, _P, _P, _P, _P, _P],
             "jvo_ilu0": [_I, _P, _P, _P, _P, _P],
             "jvo_ilu0_f32": [_I, _P, _P, _P, _P, _P],
+            "jvo_milu0": [_I, _P, _P, _P, _P, _P],
+            "jvo_milu0_f32": [_I, _P, _P, _P, _P, _P],
             "jvo_lsolve": [_I, _P, _P, _P, _P, _P, _P, _I],
             "jvo_usolve": [_I, _P, _P, _P, _P, _P, _P, _I],
             "jvo_lsolve_t": [_I, _P, _P, _P, _P, _P, _P, _I],
@@ -187,8 +189,9 @@ def permute(rowptr, colidx, perm):
 # --------------------------------------------------------------------------
 # Numeric factorisation (Sec. III, Fig. 1) and applies (Sec. VI)
 # --------------------------------------------------------------------------
-def ilu0(rowptr, colidx, vals, diag=None, dtype=np.float64):
-    """ILU(0) in place on a copy of vals; returns (lu, status, bad_row)."""
+def ilu0(rowptr, colidx, vals, diag=None, dtype=np.float64, milu=False):
+    """ILU(0) in place on a copy of vals; returns (lu, status, bad_row).
+    milu=True: modified ILU(0), dropped fill-in applied to the diagonal."""
     rowptr, colidx = _i32(rowptr), _i32(colidx)
     n = len(rowptr) - 1
     if diag is None:
@@ -197,10 +200,12 @@ def ilu0(rowptr, colidx, vals, diag=None, dtype=np.float64):
     bad = np.zeros(1, dtype=np.int32)
     if dtype == np.float32:
         a = np.array(vals, dtype=np.float32, copy=True)
-        st = _load().jvo_ilu0_f32(n, _ptr(rowptr), _ptr(colidx), _ptr(diag), _ptr(a), _ptr(bad))
+        fn = _load().jvo_milu0_f32 if milu else _load().jvo_ilu0_f32
+        st = fn(n, _ptr(rowptr), _ptr(colidx), _ptr(diag), _ptr(a), _ptr(bad))
     else:
         a = np.array(vals, dtype=np.float64, copy=True)
-        st = _load().jvo_ilu0(n, _ptr(rowptr), _ptr(colidx), _ptr(diag), _ptr(a), _ptr(bad))
+        fn = _load().jvo_milu0 if milu else _load().jvo_ilu0
+        st = fn(n, _ptr(rowptr), _ptr(colidx), _ptr(diag), _ptr(a), _ptr(bad))
     return a, st, int(bad[0])
 
 

@@ -286,6 +286,75 @@ int jvo_ilu0_f32(int n, const int *rowptr, const int *colidx, const int *diag,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Modified ILU(0) (MILU, which the up-looking design of Sec. I / Sec. III   */
+/* is said to support): the same IKJ sweep, but an update a_ij -= a_ik a_kj  */
+/* whose column j is not in row i's pattern is not dropped -- it is applied  */
+/* to the diagonal a_ii instead, at the moment it occurs (same k, same j     */
+/* order), so the diagonal absorbs every dropped fill-in and the row sums of */
+/* L U equal those of A in exact arithmetic.                                 */
+/* ------------------------------------------------------------------------ */
+int jvo_milu0(int n, const int *rowptr, const int *colidx, const int *diag,
+              double *a, int *bad_row)
+{
+    *bad_row = -1;
+    int *pos = (int *)malloc((size_t)n * sizeof(int));
+    for (int j = 0; j < n; ++j) pos[j] = -1;
+    for (int i = 0; i < n; ++i) {
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) pos[colidx[p]] = p;
+        for (int p = rowptr[i]; p < diag[i]; ++p) {
+            int k = colidx[p];
+            double lik = a[p] / a[diag[k]];
+            a[p] = lik;
+            for (int q = diag[k] + 1; q < rowptr[k + 1]; ++q) {
+                int j = colidx[q];
+                int t = pos[j] >= 0 ? pos[j] : diag[i];     /* dropped: onto a_ii */
+                a[t] = fma(-lik, a[q], a[t]);
+            }
+        }
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) pos[colidx[p]] = -1;
+        double piv = a[diag[i]];
+        if (piv == 0.0 || !isfinite(piv)) {
+            *bad_row = i;
+            free(pos);
+            return JVO_ERR_ZERO_PIVOT;
+        }
+    }
+    free(pos);
+    return JVO_OK;
+}
+
+/* MILU in binary32 (every value and operation single precision). */
+int jvo_milu0_f32(int n, const int *rowptr, const int *colidx, const int *diag,
+                  float *a, int *bad_row)
+{
+    *bad_row = -1;
+    int *pos = (int *)malloc((size_t)n * sizeof(int));
+    for (int j = 0; j < n; ++j) pos[j] = -1;
+    for (int i = 0; i < n; ++i) {
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) pos[colidx[p]] = p;
+        for (int p = rowptr[i]; p < diag[i]; ++p) {
+            int k = colidx[p];
+            float lik = a[p] / a[diag[k]];
+            a[p] = lik;
+            for (int q = diag[k] + 1; q < rowptr[k + 1]; ++q) {
+                int j = colidx[q];
+                int t = pos[j] >= 0 ? pos[j] : diag[i];
+                a[t] = fmaf(-lik, a[q], a[t]);
+            }
+        }
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) pos[colidx[p]] = -1;
+        double piv = (double)a[diag[i]];
+        if (piv == 0.0 || !isfinite(piv)) {
+            *bad_row = i;
+            free(pos);
+            return JVO_ERR_ZERO_PIVOT;
+        }
+    }
+    free(pos);
+    return JVO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Triangular solves (Sec. VI: forward and backward stri).                  */
 /* L x = b, L unit lower: x_i = b_i - sum_{j<i} l_ij x_j, rows ascending,   */
 /* the sum taken in ascending column order.                                 */

@@ -224,6 +224,85 @@ def test_ilu0_defining_property_on_pattern(seed):
     assert np.allclose(LU[mask], A[mask], rtol=1e-12, atol=1e-12)
 
 
+def _milu0_fraction(rp, ci, v):
+    """Exact-rational modified ILU(0) by right-looking (KIJ) elimination: an
+    update outside the pattern lands on the diagonal of its row instead of
+    being dropped."""
+    n = len(rp) - 1
+    S = [[False] * n for _ in range(n)]
+    A = [[Fraction(0)] * n for _ in range(n)]
+    for i in range(n):
+        for p in range(rp[i], rp[i + 1]):
+            S[i][ci[p]] = True
+            A[i][ci[p]] = Fraction(float(v[p]))
+    for k in range(n):
+        for i in range(k + 1, n):
+            if not S[i][k]:
+                continue
+            A[i][k] = A[i][k] / A[k][k]
+            for j in range(k + 1, n):
+                if S[k][j]:
+                    if S[i][j]:
+                        A[i][j] -= A[i][k] * A[k][j]
+                    else:
+                        A[i][i] -= A[i][k] * A[k][j]
+    return A, [A[i][ci[p]] for i in range(n) for p in range(rp[i], rp[i + 1])]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_milu0_matches_exact_rational_and_keeps_row_sums(seed):
+    n = 10 + seed
+    rp, ci, v = W.random_csr(n, 3.0 + seed % 3, seed=300 + seed, dominant=True)
+    lu, st, _ = O.ilu0(rp, ci, v, milu=True)
+    assert st == O.OK
+    A, exact = _milu0_fraction(rp, ci, v)
+    for got, want in zip(lu, exact):
+        assert abs(got - float(want)) <= 1e-12 * max(1.0, abs(float(want)))
+    # the exact factors keep every row sum of A: (L U) e == A e, exactly
+    Ae = [sum(Fraction(float(v[p])) for p in range(rp[i], rp[i + 1])) for i in range(n)]
+    usum = [sum(A[k][j] for j in range(k, n)) for k in range(n)]      # row sums of U
+    for i in range(n):
+        # row i of L U times e = (U e)_i + sum over k < i of l_ik (U e)_k
+        lue = usum[i] + sum(A[i][k] * usum[k] for k in range(i))
+        assert lue == Ae[i]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_milu0_defining_property(seed):
+    # off-diagonal pattern entries of L U equal A's; row sums of L U equal A's
+    rp, ci, v = W.random_csr(150, 5.0, seed=400 + seed)
+    lu, st, _ = O.ilu0(rp, ci, v, milu=True)
+    assert st == O.OK
+    L, U = _split_lu(rp, ci, lu)
+    LU = L @ U
+    A = _csr(rp, ci, v).toarray()
+    mask = _csr(rp, ci).toarray() > 0
+    np.fill_diagonal(mask, False)
+    assert np.allclose(LU[mask], A[mask], rtol=1e-12, atol=1e-12)
+    assert np.allclose(LU.sum(axis=1), A.sum(axis=1), rtol=1e-11, atol=1e-11)
+    plain, _, _ = O.ilu0(rp, ci, v)
+    assert not np.array_equal(plain, lu)          # fill-in was dropped, so MILU differs
+
+
+def test_milu0_equals_ilu0_without_fill():
+    # no update ever falls outside a tridiagonal pattern
+    n = 200
+    rp, ci, v = W.stencil((n, 1, 1), [(-1, 0, 0), (1, 0, 0)], [-1.0, -1.0], 4.0)
+    a, _, _ = O.ilu0(rp, ci, v)
+    b, _, _ = O.ilu0(rp, ci, v, milu=True)
+    assert np.array_equal(a, b)
+    a32, _, _ = O.ilu0(rp, ci, v, dtype=np.float32)
+    b32, _, _ = O.ilu0(rp, ci, v, dtype=np.float32, milu=True)
+    assert np.array_equal(a32, b32)
+
+
+def test_milu0_f32_twin_close():
+    rp, ci, v = W.lap5(12)
+    a, _, _ = O.ilu0(rp, ci, v, milu=True)
+    b, _, _ = O.ilu0(rp, ci, v, dtype=np.float32, milu=True)
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+
+
 def test_ilu0_tridiagonal_golden_pivots():
     rows = _read_golden("tridiag_pivots.txt")
     n = len(rows)
