@@ -203,7 +203,7 @@ def load_workload(name, scale, dtype):
 
 
 # --------------------------------------------------------------- CPU oracle
-def run_oracle(c, meta, dtype, budget_s):
+def run_oracle(c, meta, dtype, budget_s, milu=False):
     """The serial oracle on the same step (the factor in the step's
     precision, the solves in FP64); returns the seconds of every step run
     within the budget (at least one)."""
@@ -215,7 +215,7 @@ def run_oracle(c, meta, dtype, budget_s):
     t_end = time.perf_counter() + budget_s
     while time.perf_counter() < t_end or not times:
         t0 = time.perf_counter()
-        lu, _, _ = O.ilu0(rp, ci, v, diag, dtype=odt)
+        lu, _, _ = O.ilu0(rp, ci, v, diag, dtype=odt, milu=milu)
         y = O.lsolve(rp, ci, diag, lu, b)
         z = O.usolve(rp, ci, diag, lu, y)
         if meta["adjoint"]:
@@ -242,6 +242,7 @@ def parse_args(argv=None):
     ap.add_argument("--mode", default="syncfree", choices=["syncfree", "level"])
     ap.add_argument("--reorder", action="store_true")
     ap.add_argument("--band-rows", type=int, default=0, help="sync-free band size (0: none)")
+    ap.add_argument("--milu", action="store_true", help="modified ILU(0) factor")
     ap.add_argument("--scale", type=int, default=None, help="smaller grid (testing only)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-krylov", action="store_true")
@@ -269,11 +270,13 @@ def main(argv=None):
               "l2": "flushed before every step", "parallelism": f"replicas x{world}"}
     if a.band_rows:
         config["band_rows"] = a.band_rows
+    if a.milu:
+        config["factor"] = "MILU(0)"
 
     if a.impl == "reference":
         if rank != 0:
             return
-        times = run_oracle(c, meta, a.dtype, max(a.cpu_budget, 1.0) if a.steps else 1.0)
+        times = run_oracle(c, meta, a.dtype, max(a.cpu_budget, 1.0) if a.steps else 1.0, a.milu)
         med = statistics.median(times)
         val = step_bytes / med / 1e9
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": a.gpus,
@@ -296,7 +299,7 @@ def main(argv=None):
     rp = torch.tensor(c["rowptr"], device=dev)
     ci = torch.tensor(c["colidx"], device=dev)
     h = jv.jv_analyze(rp, ci, mode=a.mode, reorder=a.reorder, check=False,
-                      band_rows=a.band_rows)
+                      band_rows=a.band_rows, milu=a.milu)
     info = jv.jv_get_info(h)
 
     # device buffers of one step; `inputs` are what the e2e run copies in,
@@ -492,7 +495,7 @@ def main(argv=None):
 
     if rank == 0 and not a.no_cpu and world == 1:
         budget = a.cpu_budget
-        times = run_oracle(c, meta, a.dtype, budget)
+        times = run_oracle(c, meta, a.dtype, budget, a.milu)
         med = statistics.median(times)
         line["cpu_baseline"] = {"value": step_bytes / med / 1e9, "unit": "GB/s", "cores": 1,
                                 "kind": "oracle",

@@ -93,6 +93,11 @@ typedef struct {
                                        this) have finished, sleeping until then; 0 = poll from
                                        the start.  Default 1.  (The solves do not gate: on
                                        GB300 it slowed them.) */
+    int milu;                       /* 1: the handle's factor is modified ILU(0) -- an update
+                                       a_ij -= l_ik u_kj whose column j is outside row i's
+                                       pattern is applied to a_ii instead of being dropped
+                                       (row sums of L U equal A's); 0 (default): ILU(0).
+                                       Not offered with band_rows > 0 (JV_ERR_ARG). */
 } jv_options;
 
 typedef struct {

@@ -39,7 +39,8 @@ class jv_options(ctypes.Structure):
                 ("long_row", ctypes.c_int),
                 ("spin_timeout_cycles", ctypes.c_longlong), ("fault_row", ctypes.c_int),
                 ("sf_ctas_per_sm", ctypes.c_int), ("sf_backoff_ns", ctypes.c_int),
-                ("band_rows", ctypes.c_int), ("sf_gate_levels", ctypes.c_int)]
+                ("band_rows", ctypes.c_int), ("sf_gate_levels", ctypes.c_int),
+                ("milu", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
@@ -187,7 +188,7 @@ class Handle:
 
 def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_row=0,
                spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0,
-               band_rows=0, sf_gate_levels=None):
+               band_rows=0, sf_gate_levels=None, milu=False):
     """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle."""
     n = rowptr.numel() - 1
     nnz = colidx.numel()
@@ -206,6 +207,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
     opt.band_rows = int(band_rows)
     if sf_gate_levels is not None:
         opt.sf_gate_levels = int(sf_gate_levels)
+    opt.milu = int(bool(milu))
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):

@@ -122,8 +122,11 @@ __global__ void k_csc_finish(int nnz, const unsigned *col_sorted, const unsigned
 // a_rj with j > k, j in row k and in row r.  One warp per row, lanes over the
 // row's lower entries; the pairs (t = position of (r, j), q = position of
 // (k, j)) of one p are listed in ascending j, which is the order Fig. 1 applies
-// them.  Pass 1 counts (cnt[p], zero off the lower part), pass 2 fills.
-template <bool FILL>
+// them.  With MILU, a column j of row k that is not in row r gives the pair
+// (t = position of (r, r), q): the update lands on the diagonal, in the same
+// place of the order.  Pass 1 counts (cnt[p], zero off the lower part), pass
+// 2 fills.
+template <bool FILL, bool MILU>
 __global__ void k_pairs(int n, const int *rowptr, const int *colidx, const int *diag, int *cnt,
                         const int *ptr, int2 *pairs) {
     const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -136,7 +139,8 @@ __global__ void k_pairs(int n, const int *rowptr, const int *colidx, const int *
         int c = 0;
         const int base = FILL ? ptr[p] : 0;
         for (int q = diag[k] + 1; q < ke; ++q) {
-            const int t = find_col(colidx, p + 1, re, colidx[q]);
+            int t = find_col(colidx, p + 1, re, colidx[q]);
+            if (MILU && t < 0) t = rd;        // modified ILU: dropped fill onto a_ii
             if (t >= 0) {
                 if (FILL) pairs[base + c] = make_int2(t, q);
                 ++c;
@@ -404,8 +408,12 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     int *cnt = (int *)kbuf;   // nnz counts (kbuf is free again)
     JV_TRY(halloc_n(h, &h->pair_ptr, (size_t)nnz + 1));
     count_launch();
-    k_pairs<false><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(n, h->rowptr, h->colidx, h->diag,
-                                                                  cnt, nullptr, nullptr);
+    if (h->opt.milu)
+        k_pairs<false, true><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(
+            n, h->rowptr, h->colidx, h->diag, cnt, nullptr, nullptr);
+    else
+        k_pairs<false, false><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(
+            n, h->rowptr, h->colidx, h->diag, cnt, nullptr, nullptr);
     JV_CHECK_LAUNCH();
     JV_TRY(exclusive_scan_i32(cnt, h->pair_ptr, nnz, rtmp, s));
     int np = 0;
@@ -414,8 +422,12 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     h->npairs = np;
     JV_TRY(halloc_n(h, &h->pairs, (size_t)np + 1));
     count_launch();
-    k_pairs<true><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(n, h->rowptr, h->colidx, h->diag,
-                                                                 nullptr, h->pair_ptr, h->pairs);
+    if (h->opt.milu)
+        k_pairs<true, true><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(
+            n, h->rowptr, h->colidx, h->diag, nullptr, h->pair_ptr, h->pairs);
+    else
+        k_pairs<true, false><<<grid_for(n, kWarpsPerBlock), kBlock, 0, s>>>(
+            n, h->rowptr, h->colidx, h->diag, nullptr, h->pair_ptr, h->pairs);
     JV_CHECK_LAUNCH();
     JV_TRY(halloc_n(h, &h->kdiag, nnz));
     count_launch();

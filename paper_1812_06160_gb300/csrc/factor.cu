@@ -59,6 +59,7 @@ struct FactorArgs {
     long long timeout;
     unsigned backoff_ns;
     int fault_row;
+    int milu;                     // several pairs of one step may target the diagonal
 };
 
 template <class T> struct RN;
@@ -292,6 +293,8 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         }
         const TL lik = RN<TL>::div(w[p], ukk);
         const int je = fast ? send[p] : __ldg(a.pair_ptr + rs + p + 1) - j0;
+        // the targets of one step are distinct -- except, with MILU, the
+        // diagonal, which lane 0 then updates alone, in the listed order
         for (int j = jb + lane; j < je; j += kWarp) {
             int t;
             TL uq;
@@ -304,7 +307,24 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
                 const TL *src = lu + tq.y;
                 uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
             }
-            w[t] = RN<TL>::fms(lik, uq, w[t]);
+            if (!a.milu || t != nl) w[t] = RN<TL>::fms(lik, uq, w[t]);
+        }
+        if (a.milu && lane == 0) {
+            for (int j = jb; j < je; ++j) {
+                int t;
+                TL uq;
+                if (fast) {
+                    t = tgt[j];
+                    uq = uv[nl + j];
+                } else {
+                    const int2 tq = __ldg(a.pairs + j0 + j);
+                    t = tq.x - rs;
+                    if (t != nl) continue;
+                    const TL *src = lu + tq.y;
+                    uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
+                }
+                if (t == nl) w[nl] = RN<TL>::fms(lik, uq, w[nl]);
+            }
         }
         jb = je;
         __syncwarp();
@@ -418,6 +438,7 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.status = h->status;
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
+    a.milu = h->opt.milu;
     a.backoff_ns = sf_backoff(h);
     if (h->opt.mode == JV_MODE_SYNCFREE) {
         int rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
