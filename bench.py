@@ -243,6 +243,7 @@ def parse_args(argv=None):
     ap.add_argument("--reorder", action="store_true")
     ap.add_argument("--band-rows", type=int, default=0, help="sync-free band size (0: none)")
     ap.add_argument("--milu", action="store_true", help="modified ILU(0) factor")
+    ap.add_argument("--sym-levels", action="store_true", help="levels of lower(A + A^T)")
     ap.add_argument("--scale", type=int, default=None, help="smaller grid (testing only)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-krylov", action="store_true")
@@ -272,6 +273,8 @@ def main(argv=None):
         config["band_rows"] = a.band_rows
     if a.milu:
         config["factor"] = "MILU(0)"
+    if a.sym_levels:
+        config["levels"] = "lower(A+A^T)"
 
     if a.impl == "reference":
         if rank != 0:
@@ -299,7 +302,7 @@ def main(argv=None):
     rp = torch.tensor(c["rowptr"], device=dev)
     ci = torch.tensor(c["colidx"], device=dev)
     h = jv.jv_analyze(rp, ci, mode=a.mode, reorder=a.reorder, check=False,
-                      band_rows=a.band_rows, milu=a.milu)
+                      band_rows=a.band_rows, milu=a.milu, sym_levels=a.sym_levels)
     info = jv.jv_get_info(h)
 
     # device buffers of one step; `inputs` are what the e2e run copies in,

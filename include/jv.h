@@ -98,6 +98,14 @@ typedef struct {
                                        pattern is applied to a_ii instead of being dropped
                                        (row sums of L U equal A's); 0 (default): ILU(0).
                                        Not offered with band_rows > 0 (JV_ERR_ARG). */
+    int sym_levels;                 /* 1: schedule on the levels of lower(A + A^T) and
+                                       upper(A + A^T) (Sec. III's option) instead of lower(A)
+                                       and upper(A): the factor, the L and U^T solves share
+                                       the first, the U and L^T solves the second.  Results
+                                       are unchanged; with reorder = 1 the level-order
+                                       permutation then keeps A's lower/upper split for any
+                                       pattern.  0 (default).  Not offered with
+                                       band_rows > 0 (JV_ERR_ARG). */
 } jv_options;
 
 typedef struct {

@@ -40,7 +40,7 @@ class jv_options(ctypes.Structure):
                 ("spin_timeout_cycles", ctypes.c_longlong), ("fault_row", ctypes.c_int),
                 ("sf_ctas_per_sm", ctypes.c_int), ("sf_backoff_ns", ctypes.c_int),
                 ("band_rows", ctypes.c_int), ("sf_gate_levels", ctypes.c_int),
-                ("milu", ctypes.c_int)]
+                ("milu", ctypes.c_int), ("sym_levels", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
@@ -188,7 +188,7 @@ class Handle:
 
 def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_row=0,
                spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0,
-               band_rows=0, sf_gate_levels=None, milu=False):
+               band_rows=0, sf_gate_levels=None, milu=False, sym_levels=False):
     """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle."""
     n = rowptr.numel() - 1
     nnz = colidx.numel()
@@ -208,6 +208,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
     if sf_gate_levels is not None:
         opt.sf_gate_levels = int(sf_gate_levels)
     opt.milu = int(bool(milu))
+    opt.sym_levels = int(bool(sym_levels))
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):

@@ -162,12 +162,19 @@ struct Dag {
     Span cnt_beg, cnt_end;   // number of dependencies of v = cnt_end(v) - cnt_beg(v)
     Span dep_beg, dep_end;   // dependants of u: idx[dep_beg(u) .. dep_end(u))
     const int *idx;
+    // optional second part (idx2 != null): the DAG is the union of both, a
+    // dependency listed in both counted twice and removed twice -- e.g. the
+    // levels of lower(A + A^T) from the row and the column lists of A,
+    // without forming A + A^T
+    Span cnt2_beg, cnt2_end, dep2_beg, dep2_end;
+    const int *idx2;
 };
 
 __global__ void k_peel_init(int n, Dag g, int *cnt, int *lev, int *front, int *size) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = g.cnt_end.at(i) - g.cnt_beg.at(i);
+    if (g.idx2) c += g.cnt2_end.at(i) - g.cnt2_beg.at(i);
     cnt[i] = c;
     if (c == 0) {
         lev[i] = 0;
@@ -182,12 +189,15 @@ __global__ void k_peel_round(Dag g, int *cnt, int *lev, int next_level, const in
     int size = *size_in;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < size; t += gridDim.x * blockDim.x) {
         int u = fin[t];
-        int e1 = g.dep_end.at(u);
-        for (int e = g.dep_beg.at(u); e < e1; ++e) {
-            int v = g.idx[e];
-            if (atomicSub(&cnt[v], 1) == 1) {
-                lev[v] = next_level;
-                fout[atomicAdd(size_out, 1)] = v;
+        for (int part = 0; part < (g.idx2 ? 2 : 1); ++part) {
+            const int *idx = part ? g.idx2 : g.idx;
+            const int e1 = part ? g.dep2_end.at(u) : g.dep_end.at(u);
+            for (int e = part ? g.dep2_beg.at(u) : g.dep_beg.at(u); e < e1; ++e) {
+                int v = idx[e];
+                if (atomicSub(&cnt[v], 1) == 1) {
+                    lev[v] = next_level;
+                    fout[atomicAdd(size_out, 1)] = v;
+                }
             }
         }
     }
@@ -394,15 +404,36 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
                                                           h->csc2csr, h->cdiag);
     JV_CHECK_LAUNCH();
 
-    // the four DAGs
-    Dag gl{{h->rowptr, 0, 0}, {h->diag, 0, 0}, {h->cdiag, 0, 1}, {h->colptr, 1, 0}, h->rowidx};
-    Dag gu{{h->diag, 0, 1}, {h->rowptr, 1, 0}, {h->colptr, 0, 0}, {h->cdiag, 0, 0}, h->rowidx};
-    Dag gut{{h->colptr, 0, 0}, {h->cdiag, 0, 0}, {h->diag, 0, 1}, {h->rowptr, 1, 0}, h->colidx};
-    Dag glt{{h->cdiag, 0, 1}, {h->colptr, 1, 0}, {h->rowptr, 0, 0}, {h->diag, 0, 0}, h->colidx};
-    JV_TRY(build_levelset(h, JV_LOWER, gl, tmp, kbuf, vbuf, kalt, valt, rtmp));
-    JV_TRY(build_levelset(h, JV_UPPER, gu, tmp, kbuf, vbuf, kalt, valt, rtmp));
-    JV_TRY(build_levelset(h, JV_UPPER_T, gut, tmp, kbuf, vbuf, kalt, valt, rtmp));
-    JV_TRY(build_levelset(h, JV_LOWER_T, glt, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    // the four DAGs: lower(A) (factor, L solve), upper(A) (U solve), and the
+    // two transposed ones for the adjoint
+    const Span none{nullptr, 0, 0};
+    Dag gl{{h->rowptr, 0, 0}, {h->diag, 0, 0}, {h->cdiag, 0, 1}, {h->colptr, 1, 0}, h->rowidx,
+           none, none, none, none, nullptr};
+    Dag gu{{h->diag, 0, 1}, {h->rowptr, 1, 0}, {h->colptr, 0, 0}, {h->cdiag, 0, 0}, h->rowidx,
+           none, none, none, none, nullptr};
+    Dag gut{{h->colptr, 0, 0}, {h->cdiag, 0, 0}, {h->diag, 0, 1}, {h->rowptr, 1, 0}, h->colidx,
+            none, none, none, none, nullptr};
+    Dag glt{{h->cdiag, 0, 1}, {h->colptr, 1, 0}, {h->rowptr, 0, 0}, {h->diag, 0, 0}, h->colidx,
+            none, none, none, none, nullptr};
+    if (h->opt.sym_levels) {
+        // Sec. III: levels of lower(A + A^T) (and upper(A + A^T)), the union
+        // of lower(A) and lower(A^T); every structure's dependencies are a
+        // subset of one of the two, so the factor and all four solves run on
+        // them, and the level-order permutation keeps A's triangular split
+        gl.cnt2_beg = gut.cnt_beg; gl.cnt2_end = gut.cnt_end;
+        gl.dep2_beg = gut.dep_beg; gl.dep2_end = gut.dep_end; gl.idx2 = gut.idx;
+        gu.cnt2_beg = glt.cnt_beg; gu.cnt2_end = glt.cnt_end;
+        gu.dep2_beg = glt.dep_beg; gu.dep2_end = glt.dep_end; gu.idx2 = glt.idx;
+        JV_TRY(build_levelset(h, JV_LOWER, gl, tmp, kbuf, vbuf, kalt, valt, rtmp));
+        JV_TRY(build_levelset(h, JV_UPPER, gu, tmp, kbuf, vbuf, kalt, valt, rtmp));
+        h->ls[JV_UPPER_T] = h->ls[JV_LOWER];      // shares the device arrays
+        h->ls[JV_LOWER_T] = h->ls[JV_UPPER];
+    } else {
+        JV_TRY(build_levelset(h, JV_LOWER, gl, tmp, kbuf, vbuf, kalt, valt, rtmp));
+        JV_TRY(build_levelset(h, JV_UPPER, gu, tmp, kbuf, vbuf, kalt, valt, rtmp));
+        JV_TRY(build_levelset(h, JV_UPPER_T, gut, tmp, kbuf, vbuf, kalt, valt, rtmp));
+        JV_TRY(build_levelset(h, JV_LOWER_T, glt, tmp, kbuf, vbuf, kalt, valt, rtmp));
+    }
 
     // symbolic factorisation: the update pairs of every strictly lower entry
     int *cnt = (int *)kbuf;   // nnz counts (kbuf is free again)

@@ -87,6 +87,7 @@ void jv_default_options(jv_options *opt) {
     opt->sf_backoff_ns = 0;
     opt->sf_gate_levels = 1;
     opt->milu = 0;
+    opt->sym_levels = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {
@@ -107,7 +108,7 @@ int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx, const jv_op
     if (opt) h->opt = *opt; else jv_default_options(&h->opt);
     if (h->opt.mode != JV_MODE_LEVEL && h->opt.mode != JV_MODE_SYNCFREE) { delete h; return JV_ERR_ARG; }
     if (h->opt.long_row < 0 || h->opt.sf_ctas_per_sm < 0) { delete h; return JV_ERR_ARG; }
-    if (h->opt.milu && h->opt.band_rows > 0) { delete h; return JV_ERR_ARG; }
+    if ((h->opt.milu || h->opt.sym_levels) && h->opt.band_rows > 0) { delete h; return JV_ERR_ARG; }
     h->n = n;
     h->nnz = nnz;
     h->stream = static_cast<cudaStream_t>(stream);
