@@ -64,6 +64,7 @@ def _load():
             "jvo_ilu0_f32": [_I, _P, _P, _P, _P, _P],
             "jvo_milu0": [_I, _P, _P, _P, _P, _P],
             "jvo_milu0_f32": [_I, _P, _P, _P, _P, _P],
+            "jvo_iluk_symbolic": [_I, _P, _P, _I, ctypes.c_longlong, _P, _P, _P],
             "jvo_lsolve": [_I, _P, _P, _P, _P, _P, _P, _I],
             "jvo_usolve": [_I, _P, _P, _P, _P, _P, _P, _I],
             "jvo_lsolve_t": [_I, _P, _P, _P, _P, _P, _P, _I],
@@ -79,6 +80,7 @@ def _load():
             f.restype = None if name in ("jvo_bucket_levels", "jvo_transpose", "jvo_permute",
                                          "jvo_lsolve", "jvo_usolve", "jvo_lsolve_t",
                                          "jvo_usolve_t", "jvo_masked_outer", "jvo_spmv") else _I
+        lib.jvo_iluk_symbolic.restype = ctypes.c_longlong
         _lib = lib
     return _lib
 
@@ -207,6 +209,34 @@ def ilu0(rowptr, colidx, vals, diag=None, dtype=np.float64, milu=False):
         fn = _load().jvo_milu0 if milu else _load().jvo_ilu0
         st = fn(n, _ptr(rowptr), _ptr(colidx), _ptr(diag), _ptr(a), _ptr(bad))
     return a, st, int(bad[0])
+
+
+def iluk_pattern(rowptr, colidx, level):
+    """ILU(k) level-of-fill pattern: (rowptr, colidx, lev) of the filled
+    pattern, columns ascending, lev[p] the level of fill of every entry."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    n = len(rowptr) - 1
+    cap = max(2 * len(colidx), 16)
+    while True:
+        frp = np.zeros(n + 1, dtype=np.int32)
+        fci = np.zeros(cap, dtype=np.int32)
+        flev = np.zeros(cap, dtype=np.int32)
+        nz = _load().jvo_iluk_symbolic(n, _ptr(rowptr), _ptr(colidx), int(level), cap, _ptr(frp),
+                                       _ptr(fci), _ptr(flev))
+        if nz >= 0:
+            return frp, fci[:nz].copy(), flev[:nz].copy()
+        cap *= 2
+
+
+def scatter_values(rowptr, colidx, vals, frowptr, fcolidx):
+    """A's values placed on a pattern that contains A's (zeros elsewhere)."""
+    n = len(rowptr) - 1
+    out = np.zeros(len(fcolidx), dtype=np.asarray(vals).dtype)
+    for i in range(n):
+        f0, f1 = frowptr[i], frowptr[i + 1]
+        pos = np.searchsorted(fcolidx[f0:f1], colidx[rowptr[i]:rowptr[i + 1]])
+        out[f0 + pos] = vals[rowptr[i]:rowptr[i + 1]]
+    return out
 
 
 def _solve(name, rowptr, colidx, diag, lu, b):

@@ -355,6 +355,114 @@ int jvo_milu0_f32(int n, const int *rowptr, const int *colidx, const int *diag,
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILU(k) symbolic factorisation -- the level-of-fill pattern that ILU(k)     */
+/* factors on (Sec. II, and Sec. V "Incomplete levels": Javelin takes the     */
+/* pattern "with desired fill-in" and runs the same up-looking numeric sweep  */
+/* on it).  Row by row, i ascending: lev(i,j) = 0 for every entry of A's row  */
+/* i, otherwise unset; then for every column k < i of the row, in ascending   */
+/* order (fill columns included as they appear): for every column j > k of   */
+/* row k's filled pattern, lev(i,j) <- min(lev(i,j), lev(i,k) + lev(k,j) + 1) */
+/* if that is <= K.  Row i's pattern is every j with a level <= K.            */
+/* The next k is taken from a binary min-heap of the row's columns < i.       */
+/* cap bounds the output; returns the filled nnz, or -1 when cap is too      */
+/* small (the caller retries with more).                                     */
+/* ------------------------------------------------------------------------ */
+static void heap_push(int *h, int *m, int v)
+{
+    int c = (*m)++;
+    h[c] = v;
+    while (c > 0 && h[(c - 1) / 2] > h[c]) {
+        int p = (c - 1) / 2, t = h[p];
+        h[p] = h[c];
+        h[c] = t;
+        c = p;
+    }
+}
+
+static int heap_pop(int *h, int *m)
+{
+    int top = h[0];
+    h[0] = h[--(*m)];
+    int c = 0;
+    for (;;) {
+        int l = 2 * c + 1, r = l + 1, s = c;
+        if (l < *m && h[l] < h[s]) s = l;
+        if (r < *m && h[r] < h[s]) s = r;
+        if (s == c) break;
+        int t = h[s];
+        h[s] = h[c];
+        h[c] = t;
+        c = s;
+    }
+    return top;
+}
+
+static int cmp_int(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+long long jvo_iluk_symbolic(int n, const int *rowptr, const int *colidx, int K, long long cap,
+                            int *out_rowptr, int *out_colidx, int *out_lev)
+{
+    const int UNSET = -1;
+    int *lev = (int *)malloc((size_t)n * sizeof(int));
+    int *touched = (int *)malloc((size_t)n * sizeof(int));
+    int *heap = (int *)malloc((size_t)n * sizeof(int));
+    for (int j = 0; j < n; ++j) lev[j] = UNSET;
+    long long nz = 0;
+    out_rowptr[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        int nt = 0, hm = 0;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int j = colidx[p];
+            lev[j] = 0;
+            touched[nt++] = j;
+            if (j < i) heap_push(heap, &hm, j);
+        }
+        int last = -1;
+        while (hm > 0) {
+            int k = heap_pop(heap, &hm);
+            if (k == last) continue;           /* a column pushed twice */
+            last = k;
+            int lik = lev[k];
+            for (int q = out_rowptr[k]; q < out_rowptr[k + 1]; ++q) {
+                int j = out_colidx[q];
+                if (j <= k) continue;          /* row k's filled upper part */
+                int l = lik + out_lev[q] + 1;
+                if (l > K) continue;
+                if (lev[j] == UNSET) {
+                    lev[j] = l;
+                    touched[nt++] = j;
+                    if (j < i) heap_push(heap, &hm, j);
+                } else if (l < lev[j]) {
+                    lev[j] = l;
+                }
+            }
+        }
+        if (nz + nt > cap) {
+            free(lev);
+            free(touched);
+            free(heap);
+            return -1;
+        }
+        qsort(touched, (size_t)nt, sizeof(int), cmp_int);
+        for (int t = 0; t < nt; ++t) {
+            out_colidx[nz + t] = touched[t];
+            out_lev[nz + t] = lev[touched[t]];
+            lev[touched[t]] = UNSET;
+        }
+        nz += nt;
+        out_rowptr[i + 1] = (int)nz;
+    }
+    free(lev);
+    free(touched);
+    free(heap);
+    return nz;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Triangular solves (Sec. VI: forward and backward stri).                  */
 /* L x = b, L unit lower: x_i = b_i - sum_{j<i} l_ij x_j, rows ascending,   */
 /* the sum taken in ascending column order.                                 */

@@ -303,6 +303,105 @@ def test_milu0_f32_twin_close():
     assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
 
 
+# ------------------------------------------------------ ILU(k) symbolic fill
+def _fill_path_levels(rp, ci, K):
+    """Brute force by the fill-path characterisation (a different algorithm
+    from the oracle's row sweep): (i, j) has level of fill L - 1 where L is
+    the length of the shortest path i -> j in the graph of A whose
+    intermediate vertices are all numbered below min(i, j); keep L - 1 <= K."""
+    n = len(rp) - 1
+    adj = [list(ci[rp[i]:rp[i + 1]]) for i in range(n)]
+    out = {}
+    for i in range(n):
+        for j in range(n):
+            lim = min(i, j)
+            dist = {i: 0}
+            frontier = [i]
+            found = None
+            while frontier and found is None:
+                nxt = []
+                for u in frontier:
+                    for w in adj[u]:
+                        if w == j:
+                            found = dist[u] + 1
+                            break
+                        if w < lim and w not in dist:
+                            dist[w] = dist[u] + 1
+                            nxt.append(w)
+                    if found is not None:
+                        break
+                frontier = nxt
+            if i == j:
+                out[(i, j)] = 0
+            elif found is not None and found - 1 <= K:
+                out[(i, j)] = found - 1
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_iluk_pattern_matches_fill_paths(seed):
+    n = 9 + seed
+    rp, ci, _ = W.random_csr(n, 2.0 + seed % 3, seed=500 + seed)
+    for K in range(4):
+        frp, fci, flev = O.iluk_pattern(rp, ci, K)
+        got = {(i, int(fci[p])): int(flev[p]) for i in range(n) for p in range(frp[i], frp[i + 1])}
+        assert got == _fill_path_levels(rp, ci, K), (seed, K)
+
+
+def test_iluk_level_zero_is_the_pattern_of_a():
+    rp, ci, _ = W.random_csr(300, 5.0, seed=7)
+    frp, fci, flev = O.iluk_pattern(rp, ci, 0)
+    assert np.array_equal(frp, rp) and np.array_equal(fci, ci) and not flev.any()
+
+
+def test_iluk_full_fill_is_the_lu_fill_and_exact_lu():
+    # with K >= n every fill is kept: the pattern is the no-pivoting LU fill
+    # (boolean right-looking elimination) and ILU on it is exact LU
+    n = 14
+    rp, ci, v = W.random_csr(n, 2.5, seed=77, dominant=True)
+    S = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        S[i, ci[rp[i]:rp[i + 1]]] = True
+    for k in range(n):
+        for i in range(k + 1, n):
+            if S[i, k]:
+                S[i, k + 1:] |= S[k, k + 1:]
+    frp, fci, _ = O.iluk_pattern(rp, ci, n)
+    F = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        F[i, fci[frp[i]:frp[i + 1]]] = True
+    assert np.array_equal(F, S)
+    fv = O.scatter_values(rp, ci, v, frp, fci)
+    lu, st, _ = O.ilu0(frp, fci, fv)
+    assert st == O.OK
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    # dense Doolittle without pivoting, plain loops
+    U = A.copy()
+    L = np.eye(n)
+    for k in range(n):
+        for i in range(k + 1, n):
+            L[i, k] = U[i, k] / U[k, k]
+            U[i, k:] -= L[i, k] * U[k, k:]
+    dense = np.tril(L, -1) + np.triu(U)
+    got = np.zeros((n, n))
+    for i in range(n):
+        got[i, fci[frp[i]:frp[i + 1]]] = lu[frp[i]:frp[i + 1]]
+    assert np.allclose(got[F], dense[F], rtol=1e-12, atol=1e-14)
+
+
+def test_iluk_one_on_5pt_laplacian_adds_the_two_known_diagonals():
+    m = 9
+    rp, ci, _ = W.lap5(m)
+    frp, fci, flev = O.iluk_pattern(rp, ci, 1)
+    i = 4 * m + 4                                   # an interior row
+    cols = fci[frp[i]:frp[i + 1]] - i
+    assert list(cols) == [-m, -m + 1, -1, 0, 1, m - 1, m]
+    lv = dict(zip(cols, flev[frp[i]:frp[i + 1]]))
+    assert lv[-m + 1] == 1 and lv[m - 1] == 1 and lv[-1] == 0
+
+
 def test_ilu0_tridiagonal_golden_pivots():
     rows = _read_golden("tridiag_pivots.txt")
     n = len(rows)
