@@ -279,6 +279,36 @@ int jv_lsolve_noalloc(int n, const int *rowptr, const int *colidx, const int *di
                       const int *order, const double *lu, const double *b, double *x,
                       void *stream);
 
+/* ILU(k) symbolic factorisation (the level-of-fill pattern that ILU(k)
+ * factors on: Javelin runs its up-looking numeric sweep on the pattern "with
+ * desired fill-in", Sec. II / Sec. V).  Entry (i, j) is kept when its level
+ * of fill is <= level, where every entry of A has level 0 and, row by row,
+ * lev(i,j) = min over the columns k < i of row i (ascending, fill included)
+ * of lev(i,k) + lev(k,j) + 1, for j in row k's filled pattern.  ILU(k) is
+ * then: this pattern, A's values placed on it (jv_scatter_values), and
+ * jv_analyze + jv_ilu0_factor on the filled pattern.
+ * n, nnz, rowptr[n+1], colidx[nnz]: A's device CSR pattern (valid: sorted
+ * columns, diagonal present -- not re-checked here).  level >= 0.
+ * Call it twice: with fill_colidx == NULL it writes fill_rowptr[n+1]
+ * (device) and *fill_nnz (host); then, with fill_colidx (device, *fill_nnz
+ * ints) and optionally fill_level (device, *fill_nnz ints, or NULL), it
+ * writes the columns (ascending in every row) and their levels.  Each call
+ * recomputes the pattern on the GPU (rows claimed in order, every row waiting
+ * point-to-point on the rows it reads).  Synchronous; allocates and frees
+ * its own device scratch.  JV_ERR_NOMEM if a filled row exceeds 1024 entries
+ * (*bad_row, host, receives it) or the pattern exceeds 2^31 - 1 entries;
+ * JV_ERR_TIMEOUT if a wait expired. */
+int jv_iluk_symbolic(int n, int nnz, const int *rowptr, const int *colidx, int level,
+                     int *fill_rowptr, int *fill_colidx, int *fill_level, long long *fill_nnz,
+                     int *bad_row, void *stream);
+
+/* A's values on a pattern that contains A's (e.g. the ILU(k) pattern):
+ * fill_vals[q] = a_ij for the entry q = (i, j) of A, 0 elsewhere.  t: the
+ * dtype of vals and fill_vals.  All arrays device; async on stream. */
+int jv_scatter_values(int n, const int *rowptr, const int *colidx, jv_dtype t, const void *vals,
+                      const int *fill_rowptr, const int *fill_colidx, void *fill_vals,
+                      void *stream);
+
 /* Measured latency of one dependency hop, in microseconds: a value stored by
  * one SM (relaxed store, gpu scope) and seen by another SM polling it
  * (relaxed load).  In the point-to-point schedule of Sec. III-A (Fig. 4)

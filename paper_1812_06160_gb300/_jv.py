@@ -100,6 +100,9 @@ _SIGS = {
                        ctypes.POINTER(jv_krylov_info)]),
     "jv_lsolve_noalloc": (_i, [_i, _v, _v, _v, _v, _v, _v, _v, _v]),
     "jv_hop_latency": (_i, [_i, _i, ctypes.POINTER(ctypes.c_double), _v]),
+    "jv_iluk_symbolic": (_i, [_i, _i, _v, _v, _i, _v, _v, _v, ctypes.POINTER(ctypes.c_longlong),
+                              _pi, _v]),
+    "jv_scatter_values": (_i, [_i, _v, _v, _i, _v, _v, _v, _v, _v]),
     "jv_launch_count": (ctypes.c_ulonglong, []),
     "jv_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -434,6 +437,44 @@ def jv_lsolve_noalloc(rowptr, colidx, diag, order, lu, b, x=None):
         ctypes.c_void_p(torch.cuda.current_stream(b.device).cuda_stream))
     _check("jv_lsolve_noalloc", st)
     return x
+
+
+def jv_iluk_symbolic(rowptr, colidx, level, with_levels=False):
+    """ILU(k) pattern of A's CSR pattern (int32 CUDA tensors): (fill_rowptr,
+    fill_colidx[, fill_level]) as int32 CUDA tensors."""
+    n = rowptr.numel() - 1
+    rp = _dev(rowptr, "rowptr", dtype=torch.int32)
+    ci = _dev(colidx, "colidx", dtype=torch.int32)
+    frp = torch.empty(n + 1, dtype=torch.int32, device=rowptr.device)
+    nnz = ctypes.c_longlong(0)
+    bad = ctypes.c_int(-1)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(rowptr.device).cuda_stream)
+    _check("jv_iluk_symbolic", lib.jv_iluk_symbolic(n, colidx.numel(), rp, ci, int(level),
+                                                    frp.data_ptr(), None, None, ctypes.byref(nnz),
+                                                    ctypes.byref(bad), stream), bad.value)
+    fci = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=rowptr.device)
+    flev = torch.empty_like(fci) if with_levels else None
+    _check("jv_iluk_symbolic", lib.jv_iluk_symbolic(
+        n, colidx.numel(), rp, ci, int(level), frp.data_ptr(), fci.data_ptr(),
+        flev.data_ptr() if with_levels else None, ctypes.byref(nnz), ctypes.byref(bad), stream),
+        bad.value)
+    fci = fci[:nnz.value]
+    return (frp, fci, flev[:nnz.value]) if with_levels else (frp, fci)
+
+
+def jv_scatter_values(rowptr, colidx, vals, fill_rowptr, fill_colidx, out=None):
+    """A's values on the filled pattern (zeros elsewhere)."""
+    n = rowptr.numel() - 1
+    if out is None:
+        out = torch.empty(fill_colidx.numel(), dtype=vals.dtype, device=vals.device)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(vals.device).cuda_stream)
+    _check("jv_scatter_values", lib.jv_scatter_values(
+        n, _dev(rowptr, "rowptr", dtype=torch.int32), _dev(colidx, "colidx", dtype=torch.int32),
+        _dt(vals), _dev(vals, "vals", numel=colidx.numel()),
+        _dev(fill_rowptr, "fill_rowptr", dtype=torch.int32),
+        _dev(fill_colidx, "fill_colidx", dtype=torch.int32),
+        _dev(out, "out", numel=fill_colidx.numel(), dtype=vals.dtype), stream))
+    return out
 
 
 def jv_hop_latency(rounds=1000, npartners=16, device=None) -> float:

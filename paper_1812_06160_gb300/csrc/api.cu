@@ -314,6 +314,26 @@ int jv_fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu, co
     return jv::fgmres(h, vals, lu_t, lu, b, x, o ? o : &d, info);
 }
 
+int jv_iluk_symbolic(int n, int nnz, const int *rowptr, const int *colidx, int level,
+                     int *fill_rowptr, int *fill_colidx, int *fill_level, long long *fill_nnz,
+                     int *bad_row, void *stream) {
+    if (bad_row) *bad_row = -1;
+    if (n < 1 || nnz < n || !rowptr || !colidx || level < 0 || !fill_rowptr || !fill_nnz)
+        return JV_ERR_ARG;
+    return jv::iluk_symbolic(n, nnz, rowptr, colidx, level, fill_rowptr, fill_colidx, fill_level,
+                             fill_nnz, static_cast<cudaStream_t>(stream), bad_row);
+}
+
+int jv_scatter_values(int n, const int *rowptr, const int *colidx, jv_dtype t, const void *vals,
+                      const int *fill_rowptr, const int *fill_colidx, void *fill_vals,
+                      void *stream) {
+    if (n < 1 || !rowptr || !colidx || !vals || !fill_rowptr || !fill_colidx || !fill_vals ||
+        (t != JV_F64 && t != JV_F32))
+        return JV_ERR_ARG;
+    return jv::scatter_values(n, rowptr, colidx, t, vals, fill_rowptr, fill_colidx, fill_vals,
+                              static_cast<cudaStream_t>(stream));
+}
+
 int jv_hop_latency(int rounds, int npartners, double *out_us, void *stream) {
     if (rounds <= 0 || npartners <= 0 || !out_us) return JV_ERR_ARG;
     return jv::hop_latency(rounds, npartners, out_us, static_cast<cudaStream_t>(stream));

@@ -401,6 +401,11 @@ int band_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, v
 
 // trisolve.cu
 int hop_latency(int rounds, int npartners, double *out_us, cudaStream_t s);
+int iluk_symbolic(int n, int nnz, const int *rowptr, const int *colidx, int level, int *fill_rowptr,
+                  int *fill_colidx, int *fill_level, long long *fill_nnz, cudaStream_t s,
+                  int *bad_row);
+int scatter_values(int n, const int *rowptr, const int *colidx, jv_dtype t, const void *vals,
+                   const int *frowptr, const int *fcolidx, void *fvals, cudaStream_t s);
 int tri_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,
               const void *b, jv_dtype x_t, void *x, int nrhs);
 
