@@ -188,7 +188,10 @@ DAG_OF = {"factor": 0, "lsolve": 0, "usolve": 1, "usolve_t": 2, "lsolve_t": 3}
 
 
 def load_workload(name, scale, dtype):
-    c = W.config(name, scale=scale)
+    return workload_meta(W.config(name, scale=scale), dtype)
+
+
+def workload_meta(c, dtype):
     n = len(c["rowptr"]) - 1
     nnz = len(c["colidx"])
     rows = np.repeat(np.arange(n), np.diff(c["rowptr"]))
@@ -244,6 +247,8 @@ def parse_args(argv=None):
     ap.add_argument("--band-rows", type=int, default=0, help="sync-free band size (0: none)")
     ap.add_argument("--milu", action="store_true", help="modified ILU(0) factor")
     ap.add_argument("--sym-levels", action="store_true", help="levels of lower(A + A^T)")
+    ap.add_argument("--fill-level", type=int, default=0,
+                    help="ILU(k): factor on the level-k fill pattern (symbolic phase timed apart)")
     ap.add_argument("--scale", type=int, default=None, help="smaller grid (testing only)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-krylov", action="store_true")
@@ -263,6 +268,31 @@ def main(argv=None):
 
     rank, world = dist_setup(a.gpus)
     c, meta, model = load_workload(a.config, a.scale, a.dtype)
+    symbolic_ms = None
+    if a.fill_level:
+        # ILU(k): the step runs on the filled pattern, A's values scattered on
+        # it (zeros on the fill); the symbolic phase is setup, timed apart
+        if a.impl == "reference":
+            import oracle as O
+            frp, fci, _ = O.iluk_pattern(c["rowptr"], c["colidx"], a.fill_level)
+            fv = O.scatter_values(c["rowptr"], c["colidx"], c["vals"], frp, fci)
+        else:
+            import torch
+            import paper_1812_06160_gb300 as jv
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            rp0 = torch.tensor(c["rowptr"], device="cuda")
+            ci0 = torch.tensor(c["colidx"], device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            frp_d, fci_d = jv.jv_iluk_symbolic(rp0, ci0, a.fill_level)
+            e1.record()
+            torch.cuda.synchronize()
+            symbolic_ms = e0.elapsed_time(e1)
+            fv = jv.jv_scatter_values(rp0, ci0, torch.tensor(c["vals"], device="cuda"), frp_d,
+                                      fci_d).cpu().numpy()
+            frp, fci = frp_d.cpu().numpy(), fci_d.cpu().numpy()
+        c = dict(c, rowptr=frp, colidx=fci, vals=fv, name=f"{c['name']} ILU({a.fill_level})")
+        c, meta, model = workload_meta(c, a.dtype)
     n, nnz, nrhs, kernels = meta["n"], meta["nnz"], meta["nrhs"], meta["kernels"]
     step_bytes = sum(model.values())
     workload = f"{c['name']} natural-order" + (" level-reordered" if a.reorder else "")
@@ -275,6 +305,10 @@ def main(argv=None):
         config["factor"] = "MILU(0)"
     if a.sym_levels:
         config["levels"] = "lower(A+A^T)"
+    if a.fill_level:
+        config["fill_level"] = a.fill_level
+        if symbolic_ms is not None:
+            config["iluk_symbolic_ms"] = symbolic_ms
 
     if a.impl == "reference":
         if rank != 0:
