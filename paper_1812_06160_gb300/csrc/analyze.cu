@@ -152,6 +152,45 @@ __global__ void k_pairs(int n, const int *rowptr, const int *colidx, const int *
         for (int p = rd + lane; p < re; p += 32) cnt[p] = 0;
 }
 
+// step[j] = the lower entry p whose update pair j is (pairs of p: pair_ptr[p] .. pair_ptr[p+1]).
+__global__ void k_pair_step(int nnz, const int *pair_ptr, unsigned *step) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    for (int j = pair_ptr[p]; j < pair_ptr[p + 1]; ++j) step[j] = (unsigned)p;
+}
+__global__ void k_pair_target(int np, const int2 *pairs, unsigned *key, unsigned *idx) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    key[j] = (unsigned)pairs[j].x;
+    idx[j] = (unsigned)j;
+}
+__global__ void k_tpairs(int np, const unsigned *sorted_idx, const unsigned *step, const int2 *pairs,
+                         int2 *tpairs) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const unsigned j = sorted_idx[s];
+    tpairs[s] = make_int2((int)step[j], pairs[j].y);
+}
+
+// For every row: the depth of the dependency chain among its L entries (an
+// entry depends on the in-row entries whose steps update it) and whether the
+// pull form pays -- its waves (= that depth) at most half the row's steps.
+// depth[] is scratch over the row's positions.  One thread per row.
+__global__ void k_row_pull(int n, const int *rowptr, const int *diag, const int *tpair_ptr,
+                           const int2 *tpairs, int *depth, unsigned char *pull) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int rs = rowptr[r], rd = diag[r];
+    int most = 0;
+    for (int p = rs; p < rd; ++p) {
+        int d = 1;
+        for (int k = tpair_ptr[p]; k < tpair_ptr[p + 1]; ++k) d = max(d, depth[tpairs[k].x] + 1);
+        depth[p] = d;
+        most = max(most, d);
+    }
+    pull[r] = (unsigned char)(2 * most <= rd - rs ? 1 : 0);
+}
+
 __global__ void k_kdiag(int nnz, const int *colidx, const int *diag, int *kdiag) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < nnz) kdiag[p] = diag[colidx[p]];
@@ -464,6 +503,48 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     count_launch();
     k_kdiag<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, h->colidx, h->diag, h->kdiag);
     JV_CHECK_LAUNCH();
+
+    // the same pairs grouped by target: every entry's updates in ascending
+    // step (a stable sort of the step-ordered list by target), for the
+    // one-warp-per-row factor, which pulls them per entry
+    JV_TRY(halloc_n(h, &h->tpair_ptr, (size_t)nnz + 1));
+    JV_TRY(halloc_n(h, &h->tpairs, (size_t)np + 1));
+    if (np > 0) {
+        Temp ptmp;
+        unsigned *step, *pk, *pv, *pka, *pva;
+        int *prt;
+        JV_TRY(ptmp.get(&step, np));
+        JV_TRY(ptmp.get(&pk, np));
+        JV_TRY(ptmp.get(&pv, np));
+        JV_TRY(ptmp.get(&pka, np));
+        JV_TRY(ptmp.get(&pva, np));
+        JV_TRY(ptmp.get(&prt, radix_tmp_ints(np)));
+        count_launch();
+        k_pair_step<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, h->pair_ptr, step);
+        JV_CHECK_LAUNCH();
+        count_launch();
+        k_pair_target<<<grid_for(np, kBlock), kBlock, 0, s>>>(np, h->pairs, pk, pv);
+        JV_CHECK_LAUNCH();
+        JV_TRY(radix_sort_pairs(pk, pv, pka, pva, np, bits_for(nnz - 1), prt, s));
+        JV_TRY(keys_to_ptr(pk, np, h->tpair_ptr, nnz, s));
+        count_launch();
+        k_tpairs<<<grid_for(np, kBlock), kBlock, 0, s>>>(np, pv, step, h->pairs, h->tpairs);
+        JV_CHECK_LAUNCH();
+        JV_CUDA(cudaStreamSynchronize(s));
+    } else {
+        JV_CUDA(cudaMemsetAsync(h->tpair_ptr, 0, ((size_t)nnz + 1) * 4, s));
+    }
+    JV_TRY(halloc_n(h, &h->row_pull, n));
+    {
+        Temp dtmp;
+        int *depth;
+        JV_TRY(dtmp.get(&depth, nnz));
+        count_launch();
+        k_row_pull<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, h->diag, h->tpair_ptr,
+                                                          h->tpairs, depth, h->row_pull);
+        JV_CHECK_LAUNCH();
+        JV_CUDA(cudaStreamSynchronize(s));
+    }
 
     // spmv row blocks (greedy over the host copy of rowptr) and the longest row
     std::vector<int> hrp((size_t)n + 1);

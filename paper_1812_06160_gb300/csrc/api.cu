@@ -51,6 +51,7 @@ void destroy_handle(jv_handle h) {
     jv::free_workspace(h);
     jv::free_all(h);
     if (h->fscratch) cudaFree(h->fscratch);
+    if (h->pscratch) cudaFree(h->pscratch);
     if (h->ticket) cudaFree(h->ticket);
     if (h->status) cudaFree(h->status);
     if (h->h_status) cudaFreeHost(h->h_status);

@@ -60,6 +60,11 @@ struct FactorArgs {
     unsigned backoff_ns;
     int fault_row;
     int milu;                     // several pairs of one step may target the diagonal
+    const int *tpair_ptr;         // pairs by target (one-warp-per-row rows, pull form), or null
+    const int2 *tpairs;
+    void *pscratch;               // operands of rows too long for shared memory
+    long long npairs_total;       // offset of the u_kk area in pscratch
+    const unsigned char *row_pull; // per row: take the pull form
 };
 
 template <class T> struct RN;
@@ -341,11 +346,105 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     __syncwarp();                                              // shared memory reusable
 }
 
+// ------------------------------------------- one warp per row, pull form
+// Fig. 1's arithmetic regrouped by target: entry t of row r receives its
+// updates a_t -= l_p u_q (ascending step p, one fused multiply-add each) --
+// exactly the sequence the step-by-step sweep applies to it -- and an L entry
+// then divides by its u_kk.  So the L entries whose in-row producers are all
+// final can be finished together: the warp takes them 32 at a time and
+// finishes, wave after wave, every lane whose producers in the chunk are done
+// (one division sequence per wave instead of one per step); then every U
+// entry pulls its updates at once.  The row's operands (every u_q, every
+// u_kk) are read first, in parallel, each through its bounded wait, into
+// shared memory (or the operand scratch for a row too long for it).
+template <class TV, class TL, bool SF>
+__device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, unsigned gate,
+                                                 unsigned char *smem) {
+    using B = Bits<TL>;
+    const int lane = threadIdx.x & 31;
+    const int r = __ldg(a.rows + pos);
+    const int rs = __ldg(a.rowptr + r), re = __ldg(a.rowptr + r + 1), rd = __ldg(a.diag + r);
+    const int len = re - rs, nl = rd - rs;
+    const int s0 = __ldg(a.tpair_ptr + rs);
+    const int nq = __ldg(a.tpair_ptr + re) - s0;             // the row's update operands
+    TL *lu = static_cast<TL *>(a.lu);
+    const TV *vals = static_cast<const TV *>(a.vals);
+    bool fail = false;
+    const bool fast = (size_t)(len + nl + nq) * sizeof(TL) <= (size_t)kWarpSmem;
+    TL *w, *ukk, *uq;
+    if (fast) {
+        w = reinterpret_cast<TL *>(smem);
+        ukk = w + len;
+        uq = ukk + nl;
+    } else {
+        w = static_cast<TL *>(a.scratch) + rs;
+        uq = static_cast<TL *>(a.pscratch) + s0;
+        ukk = static_cast<TL *>(a.pscratch) + a.npairs_total + rs;
+    }
+    for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
+    if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
+    for (int e = lane; e < nl; e += kWarp) {
+        const TL *src = lu + __ldg(a.kdiag + rs + e);
+        ukk[e] = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
+    }
+    for (int e = lane; e < nq; e += kWarp) {
+        const TL *src = lu + __ldg(a.tpairs + s0 + e).y;
+        uq[e] = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
+    }
+    __syncwarp();
+    // L entries: chunks of 32, waves inside a chunk
+    for (int c0 = 0; c0 < nl; c0 += kWarp) {
+        const int e = c0 + lane;
+        int t0 = 0, t1 = 0;
+        bool done = e >= nl;
+        if (!done) {
+            t0 = __ldg(a.tpair_ptr + rs + e) - s0;
+            t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
+        }
+        for (unsigned dm = __ballot_sync(0xffffffffu, done); dm != 0xffffffffu;
+             dm = __ballot_sync(0xffffffffu, done)) {
+            bool ready = !done;
+            for (int k = t0; k < t1 && ready; ++k) {
+                const int pp = __ldg(a.tpairs + s0 + k).x - rs - c0;
+                if (pp >= 0) ready = (dm >> pp) & 1u;          // a producer in this chunk
+            }
+            if (ready) {
+                TL acc = w[e];
+                for (int k = t0; k < t1; ++k)
+                    acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
+                w[e] = RN<TL>::div(acc, ukk[e]);
+                done = true;
+            }
+            __syncwarp();
+        }
+    }
+    // U entries (the diagonal included): every one pulls its updates
+    for (int e = nl + lane; e < len; e += kWarp) {
+        const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
+        TL acc = w[e];
+        for (int k = t0; k < t1; ++k)
+            acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
+        w[e] = acc;
+    }
+    __syncwarp();
+    if (SF && __any_sync(0xffffffffu, fail)) return;
+    if (lane == 0) pivot_check<TL>(a, r, w[nl]);
+    for (int e = lane; e < len; e += kWarp) {
+        const TL v = w[e];
+        if (!SF || e < nl) lu[rs + e] = v;
+        else if (r != a.fault_row) publish<TL>(lu + rs + e, v);
+    }
+    __syncwarp();                                              // shared memory reusable
+}
+
 template <class TV, class TL, bool SF, int W>
 __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
     const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, task) : 0u;
-    if (hi & kLongBit) factor_warp<TV, TL, SF>(a, lo, gate, smem);
+    if (hi & kLongBit) {
+        if (a.tpairs && __ldg(a.row_pull + __ldg(a.rows + lo))) factor_warp_pull<TV, TL, SF>(a, lo, gate, smem);
+        else factor_warp<TV, TL, SF>(a, lo, gate, smem);
+    }
     else factor_lanes<TV, TL, SF, W>(a, lo, hi, gate, smem);
     __syncwarp();
 }
@@ -411,6 +510,23 @@ int run(jv_handle h, const void *vals, void *lu) {
         int rc = ensure_scratch(h);
         if (rc) return rc;
     }
+    if (W.nlong > 0) {                  // operand area of the one-warp-per-row rows
+        const size_t need = ((size_t)h->npairs + h->nnz) * sizeof(double) + 64;
+        if (h->pscratch_bytes < need) {
+            if (h->pscratch) {
+                JV_CUDA(cudaStreamSynchronize(s));
+                cudaFree(h->pscratch);
+                h->pscratch = nullptr;
+                h->pscratch_bytes = 0;
+            }
+            if (cudaMalloc(&h->pscratch, need) != cudaSuccess) {
+                cudaGetLastError();
+                h->pscratch = nullptr;
+                return JV_ERR_NOMEM;
+            }
+            h->pscratch_bytes = need;
+        }
+    }
     if (inplace) {
         void *copy = static_cast<char *>(h->fscratch) + (size_t)h->nnz * sizeof(double);
         JV_CUDA(cudaMemcpyAsync(copy, vals, (size_t)h->nnz * sizeof(TV), cudaMemcpyDeviceToDevice, s));
@@ -439,6 +555,11 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
     a.milu = h->opt.milu;
+    a.tpair_ptr = h->tpair_ptr;
+    a.tpairs = W.nlong > 0 ? h->tpairs : nullptr;
+    a.pscratch = h->pscratch;
+    a.npairs_total = h->npairs;
+    a.row_pull = h->row_pull;
     a.backoff_ns = sf_backoff(h);
     if (h->opt.mode == JV_MODE_SYNCFREE) {
         int rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);

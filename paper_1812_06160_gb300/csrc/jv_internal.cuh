@@ -332,6 +332,9 @@ struct jv_handle_s {
     int *pair_ptr = nullptr;                 // [nnz + 1], empty ranges off the strict lower part
     int2 *pairs = nullptr;                   // [npairs] (t, q) absolute CSR positions
     int *kdiag = nullptr;                    // [nnz] diag[colidx[p]]: position of u_kk for p = (r, k)
+    int *tpair_ptr = nullptr;                // [nnz + 1] the pairs grouped by target entry t:
+    int2 *tpairs = nullptr;                  // [npairs] (p, q) -- step p, operand q -- ascending p
+    unsigned char *row_pull = nullptr;       // [n] 1: a one-warp row takes the pull form
     long long npairs = 0;
     jv::Bins fbins;                          // factor work list over the levels of lower(A)
     int maxrow = 0;                          // longest row
@@ -341,6 +344,8 @@ struct jv_handle_s {
     // lazily allocated factor scratch (long rows / in-place copies)
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;
+    void *pscratch = nullptr;                // operands of long rows: [npairs + nnz] elements
+    size_t pscratch_bytes = 0;
     // scratch shared by the sync-free kernels
     unsigned *ticket = nullptr;              // [8]: next task ticket, finished CTAs, abort,
                                              // finished tasks
