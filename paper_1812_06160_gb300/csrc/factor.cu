@@ -143,6 +143,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     const int pos = lo + lane;
     bool done = pos >= hi;
     int r = 0, rs = 0, len = 0, nl = 0, m = 0, got = 0;
+    unsigned tmask = 0;                 // row-local entries some step of the row updates
     TL *lu = static_cast<TL *>(a.lu);
     if (!done) {
         r = __ldg(a.rows + pos);
@@ -167,7 +168,21 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         for (int e = 0; e < kLaneSlot; ++e) {
             if (e < len) V(e) = v[e];
             if (e < nl) { OPOS(e) = kd[e]; STEP_END(e) = (unsigned char)(se[e] - j0); }
-            if (e < np) { OPOS(nl + e) = pr[e].y; TGT(e) = (unsigned char)(pr[e].x - rs); }
+            if (e < np) {
+                OPOS(nl + e) = pr[e].y;
+                TGT(e) = (unsigned char)(pr[e].x - rs);
+                tmask |= 1u << (pr[e].x - rs);
+            }
+        }
+        // a U entry no step updates is final already: publish it now, so that
+        // only the updated ones (for a stencil, the diagonal) follow the steps
+        if (!SF || r != a.fault_row) {
+#pragma unroll
+            for (int e = 0; e < kLaneSlot; ++e)
+                if (e >= nl && e < len && !((tmask >> e) & 1u)) {
+                    if (SF) publish<TL>(lu + rs + e, v[e]);
+                    else lu[rs + e] = v[e];
+                }
         }
         if (SF && gate) {               // bring the operands' lines into L2 before sleeping
 #pragma unroll
@@ -189,11 +204,16 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             }
             V(p) = lik;
         }
-        pivot_check<TL>(a, r, V(nl));
-        for (int e = 0; e < len; ++e) {
-            if (!SF || e < nl) lu[rs + e] = V(e);
-            else if (r != a.fault_row) publish<TL>(lu + rs + e, V(e));
+        // the updated U entries, the diagonal first, then the L part
+        if (!SF || r != a.fault_row) {
+            for (int e = nl; e < len; ++e)
+                if ((tmask >> e) & 1u) {
+                    if (SF) publish<TL>(lu + rs + e, V(e));
+                    else lu[rs + e] = V(e);
+                }
         }
+        pivot_check<TL>(a, r, V(nl));
+        for (int e = 0; e < nl; ++e) lu[rs + e] = V(e);
     };
     long long t0 = 0;
     unsigned rounds = 0;
