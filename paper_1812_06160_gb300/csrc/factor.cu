@@ -218,6 +218,44 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     long long t0 = 0;
     unsigned rounds = 0;
     U u[W];
+    if (SF && __all_sync(0xffffffffu, done || m <= W)) {
+        // every operand of the row fits the window: each round polls only the
+        // operands not seen yet (a bit mask); the row is factored the round
+        // its last operand arrives
+        int op[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) op[k] = k < m ? OPOS(k) : 0;
+        unsigned seen = 0u;
+        const unsigned need = (1u << m) - 1u;
+        while (__any_sync(0xffffffffu, !done)) {
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (!done && k < m && !((seen >> k) & 1u))
+                    u[k] = ld_relaxed(reinterpret_cast<const U *>(lu + op[k]));
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (!done && k < m && !((seen >> k) & 1u) && u[k] != B::kSent) {
+                    seen |= 1u << k;
+                    V(len + k) = B::from(u[k]);
+                }
+            if (!done && seen == need) {
+                finish();
+                done = true;
+            } else if (!done) {
+                if (rounds++ == 0) t0 = clock64();
+                if ((rounds & 15u) == 0) {
+                    if (sf_aborted(a.ticket)) {
+                        done = true;                  // another wait gave up and reported
+                    } else if (clock64() - t0 > a.timeout) {
+                        report(a.status, JV_ERR_TIMEOUT, r);
+                        sf_abort(a.ticket);
+                        done = true;
+                    }
+                }
+            }
+        }
+        return;
+    }
     int wb = 0, wend = 0;
     while (__any_sync(0xffffffffu, !done)) {
         if (done) continue;
