@@ -91,8 +91,10 @@ typedef struct {
     int sf_gate_levels;             /* sync-free factor's level gate: a task polls its operands
                                        only once the tasks of all levels below (its level -
                                        this) have finished, sleeping until then; 0 = poll from
-                                       the start.  Default 1.  (The solves do not gate: on
-                                       GB300 it slowed them.) */
+                                       the start; -1 (default) = automatic: enough levels to
+                                       hold about 64 tasks, at least 1 (narrow levels want a
+                                       wider gate).  (The solves do not gate: on GB300 it
+                                       slowed them.) */
     int milu;                       /* 1: the handle's factor is modified ILU(0) -- an update
                                        a_ij -= l_ik u_kj whose column j is outside row i's
                                        pattern is applied to a_ii instead of being dropped

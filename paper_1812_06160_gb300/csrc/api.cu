@@ -86,7 +86,7 @@ void jv_default_options(jv_options *opt) {
     opt->fault_row = -1;
     opt->sf_ctas_per_sm = 0;
     opt->sf_backoff_ns = 0;
-    opt->sf_gate_levels = 1;
+    opt->sf_gate_levels = -1;
     opt->milu = 0;
     opt->sym_levels = 0;
 }

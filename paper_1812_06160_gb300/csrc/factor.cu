@@ -33,6 +33,9 @@
 // launch; the output array is the synchronisation -- lu is first filled with
 // a sentinel bit pattern, a finished row publishes each U value with one
 // store, and a dependant polls only the U values it reads.
+#include <algorithm>
+#include <cmath>
+
 #include "jv_internal.cuh"
 
 namespace jv {
@@ -604,7 +607,12 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.task_hi = W.task_hi;
     a.task_lev = W.task_lev;
     a.task_ptr = W.task_ptr;
-    a.gate_levels = h->opt.sf_gate_levels;
+    if (h->opt.sf_gate_levels >= 0) {
+        a.gate_levels = h->opt.sf_gate_levels;
+    } else {                            // automatic: about 64 tasks' worth of levels
+        const double per_level = (double)W.ntasks / (L.nlev > 0 ? L.nlev : 1);
+        a.gate_levels = (int)std::min(64.0, std::max(1.0, std::ceil(64.0 / per_level)));
+    }
     a.vals = vals;
     a.lu = lu;
     a.scratch = h->fscratch;
