@@ -54,7 +54,7 @@ KERNEL_SOURCES = {"factor": ("factor.cu", "jv_internal.cuh"),
                   "lsolve": ("trisolve.cu", "jv_internal.cuh"),
                   "usolve": ("trisolve.cu", "jv_internal.cuh")}
 TRAFFIC = {
-    ("c2", "f64", "factor", "syncfree", False): (537_022_720, "23b08de62e50"),
+    ("c2", "f64", "factor", "syncfree", False): (537_024_768, "6e3032055783"),
 }
 
 
