@@ -580,7 +580,15 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
                          cost.data() + (size_t)k * n, h->ls[k].bins));
     std::vector<int> fops((size_t)n);          // factor operands: cost minus the row's length
     for (int i = 0; i < n; ++i) fops[i] = cost[4 * (size_t)n + i] - (hrp[i + 1] - hrp[i]);
-    JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, kLaneSlot, fops.data(),
+    // the factor's one-lane slot: the wide one when many rows need 17..32
+    // words (e.g. the fill pairs of MILU), else the narrow one
+    long long mid_rows = 0;
+    for (int i = 0; i < n; ++i) {
+        const int c = cost[4 * (size_t)n + i];
+        mid_rows += (c > kLaneSlot && c <= kLaneSlotWide);
+    }
+    h->fslot = 4 * mid_rows >= n ? kLaneSlotWide : kLaneSlot;
+    JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, h->fslot, fops.data(),
                      h->fbins));
     return plan_bands(h);
 }

@@ -41,11 +41,13 @@
 namespace jv {
 namespace {
 
-// Shared memory per warp.  Lane layout: kLaneSlot values (8 B), operand
+// Shared memory per warp.  Lane layout: S (the slot, 16 or 32) values (8 B), operand
 // positions (4 B) and pair targets / step ends (1 B each) per lane, each
 // interleaved across the 32 lanes.
-constexpr int kValBytes = kWarp * kLaneSlot * 8;
-constexpr int kWarpSmem = kValBytes + kWarp * kLaneSlot * (4 + 1 + 1);
+template <int S> __host__ __device__ constexpr int val_bytes() { return kWarp * S * 8; }
+template <int S> __host__ __device__ constexpr int warp_smem() {
+    return val_bytes<S>() + kWarp * S * (4 + 1 + 1);
+}
 
 struct FactorArgs {
     const int *rowptr, *diag, *kdiag, *pair_ptr;
@@ -129,16 +131,16 @@ __device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, T d) {
 }
 
 // ------------------------------------------------------- one lane per row
-template <class TV, class TL, bool SF, int W>
+template <class TV, class TL, bool SF, int W, int S>
 __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi, unsigned gate,
                                              unsigned char *smem) {
     using B = Bits<TL>;
     using U = typename B::U;
     const int lane = threadIdx.x & 31;
     TL *vb = reinterpret_cast<TL *>(smem) + lane;
-    int *ob = reinterpret_cast<int *>(smem + kValBytes) + lane;
-    unsigned char *tb = smem + kValBytes + kWarp * kLaneSlot * 4 + lane;
-    unsigned char *eb = tb + kWarp * kLaneSlot;
+    int *ob = reinterpret_cast<int *>(smem + val_bytes<S>()) + lane;
+    unsigned char *tb = smem + val_bytes<S>() + kWarp * S * 4 + lane;
+    unsigned char *eb = tb + kWarp * S;
     auto V = [&](int e) -> TL & { return vb[e * kWarp]; };           // values, then operands
     auto OPOS = [&](int e) -> int & { return ob[e * kWarp]; };       // operand positions
     auto TGT = [&](int i) -> unsigned char & { return tb[i * kWarp]; };
@@ -157,18 +159,18 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         const int np = __ldg(a.pair_ptr + rs + nl) - j0;
         m = nl + np;
         const TV *vals = static_cast<const TV *>(a.vals);
-        TL v[kLaneSlot];
-        int kd[kLaneSlot], se[kLaneSlot];
-        int2 pr[kLaneSlot];
+        TL v[S];
+        int kd[S], se[S];
+        int2 pr[S];
 #pragma unroll
-        for (int e = 0; e < kLaneSlot; ++e) {
+        for (int e = 0; e < S; ++e) {
             if (e < len) v[e] = (TL)__ldg(vals + rs + e);
             if (e < nl) kd[e] = __ldg(a.kdiag + rs + e);
             if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
             if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
         }
 #pragma unroll
-        for (int e = 0; e < kLaneSlot; ++e) {
+        for (int e = 0; e < S; ++e) {
             if (e < len) V(e) = v[e];
             if (e < nl) { OPOS(e) = kd[e]; STEP_END(e) = (unsigned char)(se[e] - j0); }
             if (e < np) {
@@ -181,7 +183,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         // only the updated ones (for a stencil, the diagonal) follow the steps
         if (!SF || r != a.fault_row) {
 #pragma unroll
-            for (int e = 0; e < kLaneSlot; ++e)
+            for (int e = 0; e < S; ++e)
                 if (e >= nl && e < len && !((tmask >> e) & 1u)) {
                     if (SF) publish<TL>(lu + rs + e, v[e]);
                     else lu[rs + e] = v[e];
@@ -189,7 +191,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         }
         if (SF && gate) {               // bring the operands' lines into L2 before sleeping
 #pragma unroll
-            for (int e = 0; e < kLaneSlot; ++e) {
+            for (int e = 0; e < S; ++e) {
                 if (e < nl) prefetch_l2(lu + kd[e]);
                 if (e < np) prefetch_l2(lu + pr[e].y);
             }
@@ -301,7 +303,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 }
 
 // ------------------------------------------------------- one warp per row
-template <class TV, class TL, bool SF>
+template <class TV, class TL, bool SF, int S>
 __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsigned gate,
                                             unsigned char *smem) {
     using B = Bits<TL>;
@@ -317,7 +319,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     TL *lu = static_cast<TL *>(a.lu);
     const TV *vals = static_cast<const TV *>(a.vals);
     const size_t need = (size_t)(len + m) * sizeof(TL) + (size_t)(np + nl) * sizeof(int);
-    const bool fast = need <= (size_t)kWarpSmem;
+    const bool fast = need <= (size_t)warp_smem<S>();
     TL *w = fast ? reinterpret_cast<TL *>(smem) : static_cast<TL *>(a.scratch) + rs;
     TL *uv = w + len;
     int *tgt = reinterpret_cast<int *>(uv + m);                // fast path only
@@ -418,7 +420,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
 // entry pulls its updates at once.  The row's operands (every u_q, every
 // u_kk) are read first, in parallel, each through its bounded wait, into
 // shared memory (or the operand scratch for a row too long for it).
-template <class TV, class TL, bool SF>
+template <class TV, class TL, bool SF, int S>
 __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, unsigned gate,
                                                  unsigned char *smem) {
     using B = Bits<TL>;
@@ -431,7 +433,7 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     TL *lu = static_cast<TL *>(a.lu);
     const TV *vals = static_cast<const TV *>(a.vals);
     bool fail = false;
-    const bool fast = (size_t)(len + nl + nq) * sizeof(TL) <= (size_t)kWarpSmem;
+    const bool fast = (size_t)(len + nl + nq) * sizeof(TL) <= (size_t)warp_smem<S>();
     TL *w, *ukk, *uq;
     if (fast) {
         w = reinterpret_cast<TL *>(smem);
@@ -498,34 +500,36 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     __syncwarp();                                              // shared memory reusable
 }
 
-template <class TV, class TL, bool SF, int W>
+template <class TV, class TL, bool SF, int W, int S>
 __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
     const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, task) : 0u;
     if (hi & kLongBit) {
-        if (a.tpairs && __ldg(a.row_pull + __ldg(a.rows + lo))) factor_warp_pull<TV, TL, SF>(a, lo, gate, smem);
-        else factor_warp<TV, TL, SF>(a, lo, gate, smem);
+        if (a.tpairs && __ldg(a.row_pull + __ldg(a.rows + lo)))
+            factor_warp_pull<TV, TL, SF, S>(a, lo, gate, smem);
+        else
+            factor_warp<TV, TL, SF, S>(a, lo, gate, smem);
     }
-    else factor_lanes<TV, TL, SF, W>(a, lo, hi, gate, smem);
+    else factor_lanes<TV, TL, SF, W, S>(a, lo, hi, gate, smem);
     __syncwarp();
 }
 
-template <class TV, class TL, bool SF, int W>
+template <class TV, class TL, bool SF, int W, int S>
 __global__ void __launch_bounds__(kBlock, 1) k_ilu0(FactorArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int wib = threadIdx.x >> 5;
-    unsigned char *smem = dyn_smem + (size_t)wib * kWarpSmem;
+    unsigned char *smem = dyn_smem + (size_t)wib * warp_smem<S>();
     if (SF) {
         sf_for_each_task(a.ticket, a.task_end,
-                         [&](int task) { factor_task<TV, TL, SF, W>(a, task, smem); });
+                         [&](int task) { factor_task<TV, TL, SF, W, S>(a, task, smem); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-        if (task < a.task_end) factor_task<TV, TL, SF, W>(a, task, smem);
+        if (task < a.task_end) factor_task<TV, TL, SF, W, S>(a, task, smem);
     }
 }
 
-constexpr int kBlockSmem = kWarpsPerBlock * kWarpSmem;
+template <int S> constexpr int block_smem() { return kWarpsPerBlock * warp_smem<S>(); }
 
 // Scratch: [0, nnz) work area for long rows, [nnz, 2 nnz) copy of the input
 // for in-place calls (8-byte elements, enough for either dtype).
@@ -547,18 +551,22 @@ int ensure_scratch(jv_handle h) {
     return JV_OK;
 }
 
-template <class TV, class TL, bool SF, int W>
+template <class TV, class TL, bool SF, int W, int S>
 int launch_w(int grid, cudaStream_t s, const FactorArgs &a) {
-    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kBlockSmem));
+    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 block_smem<S>()));
     count_launch();
-    k_ilu0<TV, TL, SF, W><<<grid, kBlock, kBlockSmem, s>>>(a);
+    k_ilu0<TV, TL, SF, W, S><<<grid, kBlock, block_smem<S>(), s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }
 template <class TV, class TL, bool SF>
-int launch(int window, int grid, cudaStream_t s, const FactorArgs &a) {
-    return window <= 4 ? launch_w<TV, TL, SF, 4>(grid, s, a) : launch_w<TV, TL, SF, kPoll>(grid, s, a);
+int launch(int window, int slot, int grid, cudaStream_t s, const FactorArgs &a) {
+    if (slot > kLaneSlot)
+        return window <= 4 ? launch_w<TV, TL, SF, 4, kLaneSlotWide>(grid, s, a)
+                           : launch_w<TV, TL, SF, kPoll, kLaneSlotWide>(grid, s, a);
+    return window <= 4 ? launch_w<TV, TL, SF, 4, kLaneSlot>(grid, s, a)
+                       : launch_w<TV, TL, SF, kPoll, kLaneSlot>(grid, s, a);
 }
 
 template <class TV, class TL>
@@ -632,13 +640,13 @@ int run(jv_handle h, const void *vals, void *lu) {
         if (rc) return rc;
         a.task_begin = 0;
         a.task_end = W.ntasks;
-        return launch<TV, TL, true>(W.window, sf_grid(h, W.ntasks), s, a);
+        return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, W.ntasks), s, a);
     }
     for (int l = 0; l < L.nlev; ++l) {
         a.task_begin = W.h_task_ptr[l];
         a.task_end = W.h_task_ptr[l + 1];
-        int rc = launch<TV, TL, false>(W.window, grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s,
-                                       a);
+        int rc = launch<TV, TL, false>(W.window, h->fslot,
+                                       grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
         if (rc) return rc;
     }
     return JV_OK;

@@ -20,6 +20,7 @@ constexpr int kUnroll = 4;        // entries per lane per step (cooperative kern
 constexpr int kPoll = 8;          // largest poll window of the one-lane-per-row kernels
 constexpr int kLongDeps = 24;     // solve rows with more dependencies run one per warp
 constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
+constexpr int kLaneSlotWide = 32; // the same, when many rows need 17..32 (e.g. MILU fill pairs)
 constexpr int kSpmvRows = 256;    // rows per spmv block (one summing thread each)
 constexpr int kSpmvCap = 2048;    // nonzeros per spmv block (8 per thread)
 
@@ -345,6 +346,7 @@ struct jv_handle_s {
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;
     void *pscratch = nullptr;                // operands of long rows: [npairs + nnz] elements
+    int fslot = jv::kLaneSlot;               // factor one-lane slot (kLaneSlot or kLaneSlotWide)
     size_t pscratch_bytes = 0;
     // scratch shared by the sync-free kernels
     unsigned *ticket = nullptr;              // [8]: next task ticket, finished CTAs, abort,
