@@ -295,8 +295,12 @@ int jv_lsolve_noalloc(int n, const int *rowptr, const int *colidx, const int *di
  * (device) and *fill_nnz (host); then, with fill_colidx (device, *fill_nnz
  * ints) and optionally fill_level (device, *fill_nnz ints, or NULL), it
  * writes the columns (ascending in every row) and their levels.  Each call
- * recomputes the pattern on the GPU (rows claimed in order, every row waiting
- * point-to-point on the rows it reads).  Synchronous; allocates and frees
+ * recomputes the pattern on the GPU: every row on its own through the
+ * fill-path characterisation (the level of (i,j) is one less than the length
+ * of the shortest path i -> j in A's graph through vertices numbered below
+ * min(i,j)); a row whose search outgrows shared memory is redone by the
+ * row-by-row sweep above, rows claimed in order and each waiting
+ * point-to-point on the rows it reads.  Synchronous; allocates and frees
  * its own device scratch.  JV_ERR_NOMEM if a filled row exceeds 1024 entries
  * (*bad_row, host, receives it) or the pattern exceeds 2^31 - 1 entries;
  * JV_ERR_TIMEOUT if a wait expired. */

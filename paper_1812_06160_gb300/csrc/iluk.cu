@@ -8,7 +8,10 @@
 // appear), for every column j > k of row k's FILLED pattern,
 // lev(i,j) = min(lev(i,j), lev(i,k) + lev(k,j) + 1), kept when <= K.
 //
-// Row i needs the finished patterns of the rows k it meets, all k < i.  Rows
+// Two kernels.  The first computes every row on its own, from the fill-path
+// characterisation (below), with no waits.  The second -- for the rows whose
+// search outgrows the first one's tables -- runs the row sweep itself:
+// row i needs the finished patterns of the rows k it meets, all k < i.  Rows
 // are claimed in ascending order by a persistent grid, one warp per row, and
 // a row waits (bounded) on a completion word of each row k it uses -- the
 // point-to-point scheme of Sec. III-A applied to the symbolic phase.  A row's
@@ -84,6 +87,7 @@ __device__ bool await_row(const IlukArgs &a, int k, int i) {
 
 __device__ void iluk_row(const IlukArgs &a, int i, int *buf) {
     const int lane = threadIdx.x & 31;
+    if (ld_acquire_s32(a.done + i)) return;                   // computed by the path kernel
     int *col = buf, *lev = buf + kIlukCap;                    // current pattern
     int *col2 = buf + 2 * kIlukCap, *lev2 = buf + 3 * kIlukCap;  // merge target
     __shared__ int s_new[kIlukWarps][3][32];                  // (position, col, level) by rank
@@ -188,6 +192,139 @@ __global__ void __launch_bounds__(kIlukWarps * 32, 1) k_iluk(IlukArgs a) {
     sf_finish(a.ticket);
 }
 
+// ---------------------------------------------------- independent rows
+// The level of fill of (i, j) is one less than the length of the shortest
+// path i -> j in the graph of A whose intermediate vertices are all numbered
+// below min(i, j) (the fill-path characterisation of ILU(k)).  So every row
+// can be computed on its own, with no waits: a K + 1 layer dynamic program
+// over path lengths keeps, for every vertex reached by a path of length L
+// from i through vertices < i, the smallest largest-intermediate over such
+// paths; (i, w) has level L - 1 at the first L where that is below w.  Per
+// warp: three shared-memory hash tables (this layer, the next, the result),
+// then a bitonic sort of the result.  A row whose tables overflow is left to
+// the point-to-point kernel above (flagged in ovf).
+constexpr int kPathSlots = 2048;          // slots of one hash table (power of two)
+constexpr int kPathWarps = 4;             // warps per CTA: 3 tables x 2 x 8 KB each
+
+__device__ __forceinline__ bool tab_insert(int *key, int *val, int w, int m) {
+    unsigned h = ((unsigned)w * 2654435761u) >> (32 - 11);
+    for (int probe = 0; probe < kPathSlots; ++probe, h = (h + 1) & (kPathSlots - 1)) {
+        const int k = atomicCAS(key + h, -1, w);
+        if (k == -1 || k == w) {
+            atomicMin(val + h, m);
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ void iluk_row_paths(const IlukArgs &a, int i, int *sm, int *ovf) {
+    const int lane = threadIdx.x & 31;
+    int *ka = sm, *va = sm + kPathSlots;                      // layer L
+    int *kb = sm + 2 * kPathSlots, *vb = sm + 3 * kPathSlots;  // layer L + 1
+    int *kf = sm + 4 * kPathSlots, *vf = sm + 5 * kPathSlots;  // result: level of fill
+    __shared__ int s_cnt[kPathWarps];
+    __shared__ int s_bad[kPathWarps];
+    const int wib = threadIdx.x >> 5;
+    for (int t = lane; t < kPathSlots; t += 32) {
+        ka[t] = -1; va[t] = 0x7fffffff;
+        kf[t] = -1; vf[t] = 0x7fffffff;
+    }
+    if (lane == 0) s_bad[wib] = 0;
+    __syncwarp();
+    bool bad = false;
+    const int rs = __ldg(a.rowptr + i), re = __ldg(a.rowptr + i + 1);
+    for (int p = rs + lane; p < re; p += 32) {               // paths of length 1: A's row
+        const int w = __ldg(a.colidx + p);
+        bad |= !tab_insert(ka, va, w, -1);
+        bad |= !tab_insert(kf, vf, w, 0);
+    }
+    __syncwarp();
+    for (int L = 1; L <= a.K && !__any_sync(0xffffffffu, bad); ++L) {
+        for (int t = lane; t < kPathSlots; t += 32) { kb[t] = -1; vb[t] = 0x7fffffff; }
+        __syncwarp();
+        for (int t = lane; t < kPathSlots; t += 32) {
+            const int v = ka[t];
+            if (v < 0 || v >= i) continue;                     // only vertices < i lie inside
+            const int m = max(va[t], v);
+            for (int q = __ldg(a.rowptr + v); q < __ldg(a.rowptr + v + 1); ++q)
+                bad |= !tab_insert(kb, vb, __ldg(a.colidx + q), m);
+        }
+        __syncwarp();
+        for (int t = lane; t < kPathSlots; t += 32) {
+            const int w = kb[t];
+            if (w >= 0 && vb[t] < w) bad |= !tab_insert(kf, vf, w, L);
+        }
+        __syncwarp();
+        int *tk = ka, *tv = va;
+        ka = kb; va = vb; kb = tk; vb = tv;
+    }
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) atomicExch(ovf, 1);
+        return;
+    }
+    // gather the result into the other two tables' space and sort it by column
+    int *sk = ka, *sv = va;                                   // free now
+    if (lane == 0) s_cnt[wib] = 0;
+    __syncwarp();
+    for (int t = lane; t < kPathSlots; t += 32)
+        if (kf[t] >= 0) {
+            const int d = atomicAdd(&s_cnt[wib], 1);
+            sk[d] = kf[t];
+            sv[d] = vf[t];
+        }
+    __syncwarp();
+    const int c = s_cnt[wib];
+    if (c > kIlukCap) {
+        if (lane == 0) { report(a.status, JV_ERR_NOMEM, i); sf_abort(a.ticket); }
+        return;
+    }
+    int np2 = 1;
+    while (np2 < c) np2 <<= 1;
+    for (int t = c + lane; t < np2; t += 32) { sk[t] = 0x7fffffff; sv[t] = 0; }
+    __syncwarp();
+    for (int k = 2; k <= np2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < np2; t += 32) {
+                const int x = t ^ j;
+                if (x > t && ((sk[t] > sk[x]) == ((t & k) == 0))) {
+                    const int k0 = sk[t], v0 = sv[t];
+                    sk[t] = sk[x]; sv[t] = sv[x];
+                    sk[x] = k0; sv[x] = v0;
+                }
+            }
+            __syncwarp();
+        }
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(a.pool_top, (unsigned long long)c);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (off + (unsigned long long)c > a.pool_cap) {
+        if (lane == 0) { report(a.status, JV_ERR_NOMEM, -1); sf_abort(a.ticket); }
+        return;
+    }
+    for (int t = lane; t < c; t += 32) {
+        a.pool_col[off + t] = sk[t];
+        a.pool_lev[off + t] = sv[t];
+    }
+    if (lane == 0) {
+        a.row_off[i] = (int)off;
+        a.row_cnt[i] = c;
+        a.row_dpos[i] = lower_bound(sk, c, i);
+        a.done[i] = 1;                                          // computed here
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kPathWarps * 32, 1) k_iluk_paths(IlukArgs a, int *ovf) {
+    extern __shared__ __align__(16) int dyn_int[];
+    int *sm = dyn_int + (size_t)(threadIdx.x >> 5) * 6 * kPathSlots;
+    const long long nw = (long long)gridDim.x * kPathWarps;
+    for (long long i = blockIdx.x * (long long)kPathWarps + (threadIdx.x >> 5); i < a.n; i += nw) {
+        if (sf_aborted(a.ticket)) break;
+        iluk_row_paths(a, (int)i, sm, ovf);
+    }
+}
+
 // Row i of the output: copy its pool slot.
 __global__ void k_iluk_gather(int n, const int *row_off, const int *row_cnt, const int *fill_rowptr,
                               const int *pool_col, const int *pool_lev, int *out_col, int *out_lev) {
@@ -253,8 +390,13 @@ int iluk_symbolic(int n, int nnz, const int *rowptr, const int *colidx, int leve
     JV_TRY(d.get(&a.ticket, 8));
     JV_TRY(d.get(&a.status, 1));
     JV_TRY(d.get(&a.pool_top, 1));
+    int *ovf;
+    JV_TRY(d.get(&ovf, 1));
     const size_t smem = (size_t)kIlukWarps * 4 * kIlukCap * sizeof(int);
     JV_CUDA(cudaFuncSetAttribute(k_iluk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t psmem = (size_t)kPathWarps * 6 * kPathSlots * sizeof(int);
+    JV_CUDA(cudaFuncSetAttribute(k_iluk_paths, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)psmem));
     unsigned long long cap = 4ull * nnz + 2ull * n;
     for (int attempt = 0;; ++attempt) {
         Dev pool;
@@ -265,9 +407,21 @@ int iluk_symbolic(int n, int nnz, const int *rowptr, const int *colidx, int leve
         JV_CUDA(cudaMemsetAsync(a.ticket, 0, 8 * 4, s));
         JV_CUDA(cudaMemsetAsync(a.status, 0xff, 8, s));
         JV_CUDA(cudaMemsetAsync(a.pool_top, 0, 8, s));
+        JV_CUDA(cudaMemsetAsync(ovf, 0, 4, s));
+        // every row on its own; rows whose path tables overflow are left
+        // for the point-to-point kernel, which skips the rows already done
         count_launch();
-        k_iluk<<<nsm, kIlukWarps * 32, smem, s>>>(a);
+        k_iluk_paths<<<nsm, kPathWarps * 32, psmem, s>>>(a, ovf);
         JV_CHECK_LAUNCH();
+        int h_ovf = 0;
+        JV_CUDA(cudaMemcpyAsync(&h_ovf, ovf, 4, cudaMemcpyDeviceToHost, s));
+        JV_CUDA(cudaStreamSynchronize(s));
+        if (h_ovf) {
+            JV_CUDA(cudaMemsetAsync(a.ticket, 0, 8 * 4, s));
+            count_launch();
+            k_iluk<<<nsm, kIlukWarps * 32, smem, s>>>(a);
+            JV_CHECK_LAUNCH();
+        }
         unsigned long long st = 0, top = 0;
         JV_CUDA(cudaMemcpyAsync(&st, a.status, 8, cudaMemcpyDeviceToHost, s));
         JV_CUDA(cudaMemcpyAsync(&top, a.pool_top, 8, cudaMemcpyDeviceToHost, s));
