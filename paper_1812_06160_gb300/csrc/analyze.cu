@@ -340,6 +340,9 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
     JV_CUDA(cudaMemcpyAsync(rows.data(), L.rows, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
     JV_CUDA(cudaStreamSynchronize(s));
     brows.reserve(n);
+    // one-lane tasks of 32 rows where levels are wide; of 16 where they are
+    // narrow (under 2,048 rows on average), so a level spreads over more warps
+    const int per_task = (long long)n < 2048LL * L.nlev ? 16 : kWarp;
     B.h_task_ptr.assign(L.nlev + 1, 0);
     B.nlong = 0;
     for (int l = 0; l < L.nlev; ++l) {
@@ -349,9 +352,9 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
         for (int t = a; t < e; ++t)
             if (cost[rows[t]] <= threshold) brows.push_back(rows[t]);
         const int nshort = (int)brows.size() - first;
-        for (int t = 0; t < nshort; t += kWarp) {
+        for (int t = 0; t < nshort; t += per_task) {
             lo.push_back(first + t);
-            hi.push_back(first + std::min(t + kWarp, nshort));
+            hi.push_back(first + std::min(t + per_task, nshort));
         }
         for (int t = a; t < e; ++t)
             if (cost[rows[t]] > threshold) {

@@ -264,8 +264,8 @@ __device__ __forceinline__ int find_col(const int *__restrict__ col, int lo, int
 // Work list of one level structure, rows binned by cost (the row-length
 // classes of the load-balancing concern of Sec. III-A / III-B): inside every
 // level the short rows come first, in ascending order, packed 32 to a task
-// with one lane per row; every long row is a task of its own, run by the
-// whole warp.  A task never spans two levels, so the rows of a task never
+// (16 where levels are narrow) with one lane per row; every long row is a
+// task of its own, run by the whole warp.  A task never spans two levels, so the rows of a task never
 // depend on each other.
 constexpr int kLongBit = (int)0x80000000u;   // task_hi flag: one-row cooperative task
 struct Bins {
