@@ -242,7 +242,13 @@ def parse_args(argv=None):
                     help="workload (default: the 7-point 128^3 Laplacian)")
     ap.add_argument("--dtype", default=None, choices=["f64", "f32"],
                     help="factor / solve precision (default f64; f32 for c5)")
-    ap.add_argument("--mode", default="syncfree", choices=["syncfree", "level"])
+    ap.add_argument("--mode", default="syncfree", choices=["syncfree", "level", "hybrid"],
+                    help="hybrid: two-stage split, wide levels one launch each")
+    ap.add_argument("--er-corner", action="store_true",
+                    help="Even-Rows corner: the thin tail of the factor in one CTA (needs --reorder "
+                         "unless the tail is already the last rows)")
+    ap.add_argument("--stage-min-rows", type=int, default=0,
+                    help="stage test: levels with fewer rows are second-stage (0: 1024)")
     ap.add_argument("--reorder", action="store_true")
     ap.add_argument("--band-rows", type=int, default=0, help="sync-free band size (0: none)")
     ap.add_argument("--milu", action="store_true", help="modified ILU(0) factor")
@@ -257,8 +263,6 @@ def parse_args(argv=None):
     a = ap.parse_args(argv)
     if a.dtype is None:
         a.dtype = "f32" if a.config == "c5" else "f64"
-    if a.reorder and a.config == "c5":
-        ap.error("--reorder is not offered with the 32-column workload")
     return a
 
 
@@ -305,6 +309,10 @@ def main(argv=None):
         config["factor"] = "MILU(0)"
     if a.sym_levels:
         config["levels"] = "lower(A+A^T)"
+    if a.er_corner:
+        config["factor_second_stage"] = "Even-Rows corner"
+    if a.stage_min_rows:
+        config["stage_min_rows"] = a.stage_min_rows
     if a.fill_level:
         config["fill_level"] = a.fill_level
         if symbolic_ms is not None:
@@ -336,8 +344,16 @@ def main(argv=None):
     rp = torch.tensor(c["rowptr"], device=dev)
     ci = torch.tensor(c["colidx"], device=dev)
     h = jv.jv_analyze(rp, ci, mode=a.mode, reorder=a.reorder, check=False,
-                      band_rows=a.band_rows, milu=a.milu, sym_levels=a.sym_levels)
+                      band_rows=a.band_rows, milu=a.milu, sym_levels=a.sym_levels,
+                      er_corner=a.er_corner, stage_min_rows=a.stage_min_rows)
     info = jv.jv_get_info(h)
+    if a.er_corner:
+        t = 0 if a.dtype == "f64" else 1
+        config["corner_rows"] = info["corner_rows"][t]
+        config["corner_levels"] = info["corner_levels"][t]
+    if a.mode == "hybrid":
+        config["hybrid_launches"] = {"factor": info["hybrid_launches_factor"],
+                                     "solves": info["hybrid_launches"]}
 
     # device buffers of one step; `inputs` are what the e2e run copies in,
     # `outputs` what it copies back
@@ -347,6 +363,8 @@ def main(argv=None):
     if a.reorder:
         vals = jv.jv_permute_values(h, vals)
         rhs = jv.jv_permute_vector(h, rhs)
+        if g_in is not None:
+            g_in = jv.jv_permute_vector(h, g_in)
     lu = torch.empty_like(vals)
     y = torch.empty_like(rhs)
     z = torch.empty_like(rhs)

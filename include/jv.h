@@ -56,8 +56,13 @@ typedef enum { JV_F64 = 0, JV_F32 = 1 } jv_dtype;
  *           Sec. VI; rows of a level run concurrently).
  * SYNCFREE: one launch; rows are claimed in level order and each waits only
  *           on its own dependencies (the point-to-point synchronisation of
- *           Sec. III-A, Fig. 4, with per-row flags in global memory). */
-typedef enum { JV_MODE_LEVEL = 0, JV_MODE_SYNCFREE = 1 } jv_mode;
+ *           Sec. III-A, Fig. 4, with per-row flags in global memory).
+ * HYBRID:   the two-stage split of Sec. III-A (Fig. 5): levels that pass the
+ *           stage test (stage_min_rows, stage_max_density, stage_position
+ *           below) run one launch per level, and every maximal run of the
+ *           other levels -- thin or dense levels between wide ones (Fig. 6)
+ *           and the tail -- runs as one sync-free launch. */
+typedef enum { JV_MODE_LEVEL = 0, JV_MODE_SYNCFREE = 1, JV_MODE_HYBRID = 2 } jv_mode;
 
 /* The four dependency structures built by jv_analyze.
  * LOWER:   lower(A), forward solve and factor (Sec. III: levels of lower(A)).
@@ -108,6 +113,32 @@ typedef struct {
                                        permutation then keeps A's lower/upper split for any
                                        pattern.  0 (default).  Not offered with
                                        band_rows > 0 (JV_ERR_ARG). */
+    /* Stage test of the two-stage schedules (Sec. III-A: minimal rows per
+       level, row density, relative position).  A level belongs to the upper
+       stage when it has at least stage_min_rows rows, its mean row length is
+       at most stage_max_density times the matrix's mean, and it starts before
+       row stage_position * n of the level order; every other level is
+       second-stage material.  Used by JV_MODE_HYBRID and er_corner. */
+    int stage_min_rows;             /* 0 = default (1024) */
+    double stage_max_density;       /* 0 = no density limit (default) */
+    double stage_position;          /* 0 = no position limit (default); in (0, 1] */
+    int er_corner;                  /* 1: Even-Rows second stage for the factor (Sec. III-B,
+                                       Fig. 8).  The corner is the tail of levels of lower(A)
+                                       that starts where every later level is second-stage
+                                       material, shortened from its top until it fits one
+                                       CTA's shared memory.  The upper stage (mode LEVEL,
+                                       SYNCFREE or HYBRID) factors the rows above it; then
+                                       one CTA runs FACTOR_L -- every corner row's updates
+                                       from the rows above the corner, all rows at once --
+                                       and factors the corner level by level in shared
+                                       memory.  Each row still takes its updates in
+                                       ascending column order, so the factor is ILU(0)'s
+                                       exactly.  The corner's rows must be the last rows of
+                                       the handle's order (reorder = 1 guarantees it; else
+                                       JV_ERR_ARG); a tail too large for shared memory leaves
+                                       the corner empty (jv_info.corner_rows = 0).  Not
+                                       offered with band_rows > 0 (JV_ERR_ARG).  0 = off
+                                       (default). */
 } jv_options;
 
 typedef struct {
@@ -122,6 +153,12 @@ typedef struct {
     long long npairs;           /* update pairs of the symbolic factorisation (flops of the
                                    factor = 2 npairs + nnz_lower) */
     int mode, reorder;
+    int hybrid_launches[4];     /* launches of a JV_MODE_HYBRID solve per jv_structure
+                                   (one per upper-stage level + one per sync-free run) */
+    int hybrid_launches_factor; /* the same for an FP64 factor (levels above its corner) */
+    int corner_rows[2];         /* rows of the Even-Rows corner per factor jv_dtype (the
+                                   FP32 corner holds about twice the rows); 0: none */
+    int corner_levels[2];       /* levels of lower(A) each corner spans */
 } jv_info;
 
 /* Fill *opt with the defaults above. */
@@ -149,7 +186,9 @@ int jv_last_bad_row(void);
 /* Release every device array the handle owns.  NULL is ignored. */
 void jv_destroy(jv_handle h);
 
-/* Change the handle's stream (cudaStream_t) / scheduling mode / check flag. */
+/* Change the handle's stream (cudaStream_t) / scheduling mode (any jv_mode:
+ * the stage test and the corner are planned by jv_analyze whatever the mode)
+ * / check flag. */
 int jv_set_stream(jv_handle h, void *stream);
 int jv_set_mode(jv_handle h, int mode);
 int jv_set_check(jv_handle h, int check);

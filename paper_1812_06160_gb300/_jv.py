@@ -29,7 +29,8 @@ JV_ERR_INTERNAL = -8
 JV_ERR_NOT_CONVERGED = -9
 
 JV_F64, JV_F32 = 0, 1
-JV_MODE_LEVEL, JV_MODE_SYNCFREE = 0, 1
+JV_MODE_LEVEL, JV_MODE_SYNCFREE, JV_MODE_HYBRID = 0, 1, 2
+MODES = {"level": JV_MODE_LEVEL, "syncfree": JV_MODE_SYNCFREE, "hybrid": JV_MODE_HYBRID}
 JV_LOWER, JV_UPPER, JV_UPPER_T, JV_LOWER_T = 0, 1, 2, 3
 STRUCTURES = {"L": JV_LOWER, "U": JV_UPPER, "Ut": JV_UPPER_T, "Lt": JV_LOWER_T}
 
@@ -40,7 +41,9 @@ class jv_options(ctypes.Structure):
                 ("spin_timeout_cycles", ctypes.c_longlong), ("fault_row", ctypes.c_int),
                 ("sf_ctas_per_sm", ctypes.c_int), ("sf_backoff_ns", ctypes.c_int),
                 ("band_rows", ctypes.c_int), ("sf_gate_levels", ctypes.c_int),
-                ("milu", ctypes.c_int), ("sym_levels", ctypes.c_int)]
+                ("milu", ctypes.c_int), ("sym_levels", ctypes.c_int),
+                ("stage_min_rows", ctypes.c_int), ("stage_max_density", ctypes.c_double),
+                ("stage_position", ctypes.c_double), ("er_corner", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
@@ -48,7 +51,9 @@ class jv_info(ctypes.Structure):
                 ("nnz_upper", ctypes.c_int), ("nlev", ctypes.c_int * 4),
                 ("nlong", ctypes.c_int * 4), ("nlong_factor", ctypes.c_int),
                 ("band_rows", ctypes.c_int * 4), ("nband_levels", ctypes.c_int * 4),
-                ("npairs", ctypes.c_longlong), ("mode", ctypes.c_int), ("reorder", ctypes.c_int)]
+                ("npairs", ctypes.c_longlong), ("mode", ctypes.c_int), ("reorder", ctypes.c_int),
+                ("hybrid_launches", ctypes.c_int * 4), ("hybrid_launches_factor", ctypes.c_int),
+                ("corner_rows", ctypes.c_int * 2), ("corner_levels", ctypes.c_int * 2)]
 
 
 class jv_krylov_opts(ctypes.Structure):
@@ -191,15 +196,20 @@ class Handle:
 
 def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_row=0,
                spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0,
-               band_rows=0, sf_gate_levels=None, milu=False, sym_levels=False):
-    """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle."""
+               band_rows=0, sf_gate_levels=None, milu=False, sym_levels=False,
+               stage_min_rows=0, stage_max_density=0.0, stage_position=0.0, er_corner=False):
+    """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle.
+    ``mode``: "level", "syncfree" or "hybrid" (the two-stage split of Sec. III-A,
+    with the stage test ``stage_min_rows`` / ``stage_max_density`` /
+    ``stage_position``); ``er_corner``: Even-Rows second stage of the factor
+    (Sec. III-B)."""
     n = rowptr.numel() - 1
     nnz = colidx.numel()
     rp = _dev(rowptr, "rowptr", dtype=torch.int32)
     ci = _dev(colidx, "colidx", dtype=torch.int32)
     opt = jv_options()
     lib.jv_default_options(ctypes.byref(opt))
-    opt.mode = {"level": JV_MODE_LEVEL, "syncfree": JV_MODE_SYNCFREE}[mode]
+    opt.mode = MODES[mode]
     opt.reorder = int(bool(reorder))
     opt.check = int(bool(check))
     opt.long_row = int(long_row)
@@ -212,6 +222,10 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
         opt.sf_gate_levels = int(sf_gate_levels)
     opt.milu = int(bool(milu))
     opt.sym_levels = int(bool(sym_levels))
+    opt.stage_min_rows = int(stage_min_rows)
+    opt.stage_max_density = float(stage_max_density)
+    opt.stage_position = float(stage_position)
+    opt.er_corner = int(bool(er_corner))
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):
@@ -226,7 +240,7 @@ def jv_destroy(h: Handle):
 
 
 def jv_set_mode(h: Handle, mode: str):
-    _check("jv_set_mode", lib.jv_set_mode(h.ptr, {"level": 0, "syncfree": 1}[mode]))
+    _check("jv_set_mode", lib.jv_set_mode(h.ptr, MODES[mode]))
 
 
 def jv_set_check(h: Handle, check: bool):
@@ -334,7 +348,10 @@ def jv_get_info(h):
     return dict(n=info.n, nnz=info.nnz, nnz_lower=info.nnz_lower, nnz_upper=info.nnz_upper,
                 nlev=list(info.nlev), nlong=list(info.nlong), nlong_factor=info.nlong_factor,
                 band_rows=list(info.band_rows), nband_levels=list(info.nband_levels),
-                npairs=info.npairs, mode=info.mode, reorder=info.reorder)
+                npairs=info.npairs, mode=info.mode, reorder=info.reorder,
+                hybrid_launches=list(info.hybrid_launches),
+                hybrid_launches_factor=info.hybrid_launches_factor,
+                corner_rows=list(info.corner_rows), corner_levels=list(info.corner_levels))
 
 
 def jv_get_levels(h, which="L"):

@@ -638,13 +638,15 @@ void free_all(jv_handle h) {
     h->allocs.clear();
     for (auto &L : h->ls) L = LevelSet();
     h->fbins = Bins();
+    for (auto &C : h->corner) C = CornerPlan();
 }
 
 int analyze(jv_handle h, const int *rowptr, const int *colidx) {
     const int n = h->n, nnz = h->nnz;
     cudaStream_t s = h->stream;
     int rc = build_all(h, rowptr, colidx);
-    if (rc != JV_OK || !h->opt.reorder) return rc;
+    if (rc != JV_OK) return rc;
+    if (!h->opt.reorder) return plan_stages(h);
 
     // B = P A P^T with P the level order of lower(A)
     Temp tmp;
@@ -701,7 +703,7 @@ int analyze(jv_handle h, const int *rowptr, const int *colidx) {
     JV_CUDA(cudaMemcpyAsync(h->iperm, iperm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     JV_CUDA(cudaMemcpyAsync(h->vmap, vmap, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
     JV_CUDA(cudaStreamSynchronize(s));
-    return JV_OK;
+    return plan_stages(h);
 }
 
 }  // namespace jv

@@ -89,6 +89,10 @@ void jv_default_options(jv_options *opt) {
     opt->sf_gate_levels = -1;
     opt->milu = 0;
     opt->sym_levels = 0;
+    opt->stage_min_rows = 0;
+    opt->stage_max_density = 0.0;
+    opt->stage_position = 0.0;
+    opt->er_corner = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {
@@ -107,9 +111,21 @@ int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx, const jv_op
     if (n < 1 || nnz < n || !rowptr || !colidx) return JV_ERR_ARG;
     jv_handle h = new jv_handle_s();
     if (opt) h->opt = *opt; else jv_default_options(&h->opt);
-    if (h->opt.mode != JV_MODE_LEVEL && h->opt.mode != JV_MODE_SYNCFREE) { delete h; return JV_ERR_ARG; }
+    if (h->opt.mode != JV_MODE_LEVEL && h->opt.mode != JV_MODE_SYNCFREE && h->opt.mode != JV_MODE_HYBRID) {
+        delete h;
+        return JV_ERR_ARG;
+    }
     if (h->opt.long_row < 0 || h->opt.sf_ctas_per_sm < 0) { delete h; return JV_ERR_ARG; }
-    if ((h->opt.milu || h->opt.sym_levels) && h->opt.band_rows > 0) { delete h; return JV_ERR_ARG; }
+    if ((h->opt.milu || h->opt.sym_levels || h->opt.er_corner) && h->opt.band_rows > 0) {
+        delete h;
+        return JV_ERR_ARG;
+    }
+    if (h->opt.stage_min_rows < 0 || h->opt.stage_max_density < 0 || h->opt.stage_position < 0 ||
+        h->opt.stage_position > 1 || !(h->opt.stage_max_density == h->opt.stage_max_density) ||
+        !(h->opt.stage_position == h->opt.stage_position)) {
+        delete h;
+        return JV_ERR_ARG;
+    }
     h->n = n;
     h->nnz = nnz;
     h->stream = static_cast<cudaStream_t>(stream);
@@ -153,7 +169,8 @@ int jv_set_stream(jv_handle h, void *stream) {
 }
 
 int jv_set_mode(jv_handle h, int mode) {
-    if (!h || (mode != JV_MODE_LEVEL && mode != JV_MODE_SYNCFREE)) return JV_ERR_ARG;
+    if (!h || (mode != JV_MODE_LEVEL && mode != JV_MODE_SYNCFREE && mode != JV_MODE_HYBRID))
+        return JV_ERR_ARG;
     h->opt.mode = mode;
     return JV_OK;
 }
@@ -243,6 +260,14 @@ int jv_get_info(jv_handle h, jv_info *info) {
     info->npairs = h->npairs;
     info->mode = h->opt.mode;
     info->reorder = h->opt.reorder;
+    for (int k = 0; k < 4; ++k) info->hybrid_launches[k] = jv::hybrid_launches(h->ls[k], h->ls[k].nlev);
+    info->hybrid_launches_factor = jv::hybrid_launches(h->ls[JV_LOWER], h->corner[JV_F64].use
+                                                                            ? h->corner[JV_F64].K
+                                                                            : h->ls[JV_LOWER].nlev);
+    for (int t = 0; t < 2; ++t) {
+        info->corner_rows[t] = h->corner[t].use ? h->corner[t].R : 0;
+        info->corner_levels[t] = h->corner[t].use ? h->corner[t].nl : 0;
+    }
     return JV_OK;
 }
 

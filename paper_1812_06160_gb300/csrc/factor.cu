@@ -503,7 +503,7 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
 template <class TV, class TL, bool SF, int W, int S>
 __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
-    const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, task) : 0u;
+    const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, a.task_begin, task) : 0u;
     if (hi & kLongBit) {
         if (a.tpairs && __ldg(a.row_pull + __ldg(a.rows + lo)))
             factor_warp_pull<TV, TL, SF, S>(a, lo, gate, smem);
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_ilu0(FactorArgs a) {
     const int wib = threadIdx.x >> 5;
     unsigned char *smem = dyn_smem + (size_t)wib * warp_smem<S>();
     if (SF) {
-        sf_for_each_task(a.ticket, a.task_end,
+        sf_for_each_task(a.ticket, a.task_begin, a.task_end,
                          [&](int task) { factor_task<TV, TL, SF, W, S>(a, task, smem); });
         sf_finish(a.ticket);
     } else {
@@ -635,21 +635,42 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.npairs_total = h->npairs;
     a.row_pull = h->row_pull;
     a.backoff_ns = sf_backoff(h);
-    if (h->opt.mode == JV_MODE_SYNCFREE) {
-        int rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
-        if (rc) return rc;
-        a.task_begin = 0;
-        a.task_end = W.ntasks;
-        return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, W.ntasks), s, a);
-    }
-    for (int l = 0; l < L.nlev; ++l) {
+    // the upper stage: levels [0, lend), above the Even-Rows corner if any
+    const jv_dtype lu_t = sizeof(TL) == 8 ? JV_F64 : JV_F32;
+    const CornerPlan &C = h->corner[lu_t];
+    const int lend = C.use ? C.K : L.nlev;
+    auto one_level = [&](int l) {
         a.task_begin = W.h_task_ptr[l];
         a.task_end = W.h_task_ptr[l + 1];
-        int rc = launch<TV, TL, false>(W.window, h->fslot,
-                                       grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+        return launch<TV, TL, false>(W.window, h->fslot,
+                                     grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+    };
+    auto sync_free = [&](int l0, int l1) {
+        a.task_begin = W.h_task_ptr[l0];
+        a.task_end = W.h_task_ptr[l1];
+        if (a.task_end <= a.task_begin) return (int)JV_OK;
+        return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, a.task_end - a.task_begin), s, a);
+    };
+    int rc = JV_OK;
+    if (h->opt.mode != JV_MODE_LEVEL) {
+        rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
         if (rc) return rc;
     }
-    return JV_OK;
+    if (h->opt.mode == JV_MODE_SYNCFREE) {
+        rc = sync_free(0, lend);
+    } else if (h->opt.mode == JV_MODE_LEVEL) {
+        for (int l = 0; l < lend && rc == JV_OK; ++l) rc = one_level(l);
+    } else {
+        for (const Seg &g : L.segs) {
+            if (g.l0 >= lend || rc != JV_OK) break;
+            const int l1 = std::min(g.l1, lend);
+            if (g.sf) rc = sync_free(g.l0, l1);
+            else for (int l = g.l0; l < l1 && rc == JV_OK; ++l) rc = one_level(l);
+        }
+    }
+    if (rc) return rc;
+    // the second stage: Even-Rows corner
+    return corner_factor(h, sizeof(TV) == 8 ? JV_F64 : JV_F32, vals, lu_t, lu);
 }
 
 }  // namespace

@@ -188,7 +188,7 @@ __device__ void iluk_row(const IlukArgs &a, int i, int *buf) {
 __global__ void __launch_bounds__(kIlukWarps * 32, 1) k_iluk(IlukArgs a) {
     extern __shared__ __align__(16) int dyn_int[];
     int *buf = dyn_int + (size_t)(threadIdx.x >> 5) * 4 * kIlukCap;
-    sf_for_each_task(a.ticket, a.n, [&](int i) { iluk_row(a, i, buf); });
+    sf_for_each_task(a.ticket, 0, a.n, [&](int i) { iluk_row(a, i, buf); });
     sf_finish(a.ticket);
 }
 

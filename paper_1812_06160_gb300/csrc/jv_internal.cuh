@@ -141,21 +141,23 @@ __device__ __forceinline__ void sf_pause(unsigned it, unsigned max_ns) {
 // task starts and read when it ends, so its latency hides behind the task.
 // Every task waits only on tasks of lower index, each claimed by a resident
 // warp (a warp's pending claim is above its current task), so the lowest
-// unfinished task always runs: no deadlock.  Warp-uniform; lanes must be
-// converged.
+// unfinished task always runs: no deadlock.  The launch covers tasks
+// [begin, end): a launch over a later range of levels (the two-stage
+// schedules) finds the rows of earlier ranges already written by the launches
+// before it.  Warp-uniform; lanes must be converged.
 template <class F>
-__device__ __forceinline__ void sf_for_each_task(unsigned *ticket, int ntasks, F &&run) {
+__device__ __forceinline__ void sf_for_each_task(unsigned *ticket, int begin, int end, F &&run) {
     const int lane = threadIdx.x & (kWarp - 1);
     unsigned claim = 0;
     if (lane == 0) claim = atomicAdd(ticket, 1u);
-    int task = __shfl_sync(0xffffffffu, (int)claim, 0);
-    while (task < ntasks) {
+    int task = begin + __shfl_sync(0xffffffffu, (int)claim, 0);
+    while (task < end) {
         unsigned next = 0;
         if (lane == 0) next = atomicAdd(ticket, 1u);
         run(task);
         __syncwarp();
         if (lane == 0) atomicAdd(ticket + 3, 1u);        // finished tasks (level gate)
-        task = __shfl_sync(0xffffffffu, (int)next, 0);
+        task = begin + __shfl_sync(0xffffffffu, (int)next, 0);
     }
 }
 
@@ -187,12 +189,14 @@ __device__ __forceinline__ void sf_abort(unsigned *ticket) { atomicExch(ticket +
 // hint, never a correctness condition (every operand is still awaited on its
 // own word); it reaches the gate because the tasks below it wait on nothing
 // above.  Bounded by the wait bound, after which the task simply polls.
-// Warp-uniform.
+// The count starts at the launch's first task `begin`.  Warp-uniform.
 __device__ __forceinline__ unsigned sf_gate_of(const int *task_lev, const int *task_ptr,
-                                               int gate_levels, int task) {
+                                               int gate_levels, int begin, int task) {
     if (gate_levels <= 0) return 0u;
     const int l = __ldg(task_lev + task) - gate_levels;
-    return l > 0 ? (unsigned)__ldg(task_ptr + l) : 0u;
+    if (l <= 0) return 0u;
+    const int g = __ldg(task_ptr + l) - begin;
+    return g > 0 ? (unsigned)g : 0u;
 }
 __device__ __forceinline__ void sf_gate_wait(unsigned *ticket, unsigned gate, long long timeout) {
     unsigned c = ld_relaxed(ticket + 3);
@@ -282,6 +286,35 @@ struct Bins {
     std::vector<int> h_task_ptr;  // [nlev+1] first task of every level
 };
 
+// Two-stage schedules.  A run of levels [l0, l1) of one level structure:
+// one launch per level (upper-stage levels of the hybrid schedule) or one
+// sync-free launch over the run (every maximal run of second-stage levels).
+struct Seg {
+    int l0, l1;
+    bool sf;
+};
+
+// Even-Rows corner of the factor (Sec. III-B, Fig. 8): the levels [K, nlev)
+// of lower(A), whose rows are the last rows [c, n) of the handle's order, so
+// their entries are the CSR tail [E0, nnz).  One CTA holds the corner's
+// values in shared memory, applies every row's updates from the rows above
+// the corner (FACTOR_L), then factors the corner level by level.  The level
+// loop reads a per-row program of 16-bit shared-memory offsets, in level
+// order: [row - c, steps, diagonal] then per step [entry, u_kk, pairs] and
+// per pair [target, operand] -- the step's updates in their stored order.
+struct CornerPlan {
+    bool use = false;
+    int K = 0, nl = 0;          // first level, levels
+    int c = 0, R = 0;           // first row, rows
+    int E0 = 0, E = 0;          // first CSR position, entries
+    int words = 0;              // program words
+    size_t smem = 0;            // shared memory of the launch
+    int *prog_ptr = nullptr;    // [R+1] first word of every row (level order)
+    int *lvl_ptr = nullptr;     // [nl+1] first row of every corner level
+    unsigned short *prog = nullptr;  // [words] (padded to an even count)
+};
+constexpr int kCornerThreads = 1024;
+
 // Band schedule of one level structure: rows split into nb contiguous bands
 // of B rows (natural order); inside a band, rows are grouped by their local
 // level -- the longest path through dependencies that stay inside the band.
@@ -309,6 +342,8 @@ struct LevelSet {
     std::vector<int> h_ptr;    // host copy of ptr
     Bins bins;                 // single right-hand-side solve work list
     BandPlan band;
+    std::vector<Seg> segs;     // hybrid schedule over [0, nlev)
+    int tail = 0;              // first level after which every level is second-stage
 };
 
 struct Workspace;  // Krylov scratch, krylov.cu
@@ -338,6 +373,7 @@ struct jv_handle_s {
     unsigned char *row_pull = nullptr;       // [n] 1: a one-warp row takes the pull form
     long long npairs = 0;
     jv::Bins fbins;                          // factor work list over the levels of lower(A)
+    jv::CornerPlan corner[2];                // Even-Rows corner per factor dtype (jv_dtype)
     int maxrow = 0;                          // longest row
     // spmv row blocks: block b covers rows [spmv_blk[b], spmv_blk[b+1])
     int *spmv_blk = nullptr;
@@ -405,6 +441,12 @@ int band_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dty
                const void *b, jv_dtype x_t, void *x);
 int band_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu,
                 void *scratch);
+
+// stages.cu: stage test, hybrid segments, Even-Rows corner
+int plan_stages(jv_handle h);
+int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu);
+// launches of a hybrid run over levels [0, lend) of structure s (per-level tasks)
+int hybrid_launches(const LevelSet &L, int lend);
 
 // trisolve.cu
 int hop_latency(int rounds, int npartners, double *out_us, cudaStream_t s);

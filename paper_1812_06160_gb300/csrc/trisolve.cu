@@ -329,7 +329,7 @@ template <class TL, class TB, class TX, bool SF, int W, bool ONE>
 __global__ void __launch_bounds__(kBlock, 1) k_trsv(TriArgs a) {
     const int wib = threadIdx.x >> 5;
     if (SF) {
-        sf_for_each_task(a.ticket, a.task_end,
+        sf_for_each_task(a.ticket, a.task_begin, a.task_end,
                          [&](int task) { trsv_task<TL, TB, TX, SF, W, ONE>(a, task); });
         sf_finish(a.ticket);
     } else {
@@ -388,7 +388,7 @@ template <class TL, class TB, class TX, bool SF>
 __global__ void __launch_bounds__(kBlock) k_trsm(TriArgs a) {
     const int wib = threadIdx.x >> 5;
     if (SF) {
-        sf_for_each_task(a.ticket, a.task_end, [&](int task) { trsm_task<TL, TB, TX, SF>(a, task); });
+        sf_for_each_task(a.ticket, a.task_begin, a.task_end, [&](int task) { trsm_task<TL, TB, TX, SF>(a, task); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
@@ -447,21 +447,38 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
     a.backoff_ns = sf_backoff(h);
-    if (h->opt.mode == JV_MODE_SYNCFREE) {
-        int rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
+    // tasks of levels [l0, l1): rows (several right-hand sides) or work-list tasks
+    auto tasks = [&](int l0, int l1) {
+        a.task_begin = multi ? L.h_ptr[l0] : W.h_task_ptr[l0];
+        a.task_end = multi ? L.h_ptr[l1] : W.h_task_ptr[l1];
+    };
+    auto one_level = [&](int l) {
+        tasks(l, l + 1);
+        return launch<TL, TB, TX, false>(multi, W.window,
+                                         grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+    };
+    auto sync_free = [&](int l0, int l1) {
+        tasks(l0, l1);
+        if (a.task_end <= a.task_begin) return (int)JV_OK;
+        return launch<TL, TB, TX, true>(multi, W.window, sf_grid(h, a.task_end - a.task_begin), s, a);
+    };
+    int rc = JV_OK;
+    if (h->opt.mode != JV_MODE_LEVEL) {
+        rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
         if (rc) return rc;
-        a.task_begin = 0;
-        a.task_end = multi ? h->n : W.ntasks;
-        return launch<TL, TB, TX, true>(multi, W.window, sf_grid(h, a.task_end), s, a);
     }
-    for (int l = 0; l < L.nlev; ++l) {
-        a.task_begin = multi ? L.h_ptr[l] : W.h_task_ptr[l];
-        a.task_end = multi ? L.h_ptr[l + 1] : W.h_task_ptr[l + 1];
-        int rc = launch<TL, TB, TX, false>(multi, W.window,
-                                           grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
-        if (rc) return rc;
+    if (h->opt.mode == JV_MODE_SYNCFREE) return sync_free(0, L.nlev);
+    if (h->opt.mode == JV_MODE_LEVEL) {
+        for (int l = 0; l < L.nlev && rc == JV_OK; ++l) rc = one_level(l);
+        return rc;
     }
-    return JV_OK;
+    // hybrid: upper-stage levels one launch each, second-stage runs sync-free
+    for (const Seg &g : L.segs) {
+        if (rc != JV_OK) break;
+        if (g.sf) rc = sync_free(g.l0, g.l1);
+        else for (int l = g.l0; l < g.l1 && rc == JV_OK; ++l) rc = one_level(l);
+    }
+    return rc;
 }
 
 }  // namespace

@@ -63,3 +63,11 @@ def test_binding_option_struct_layout(lib):
     lib.jv_default_krylov_opts(ctypes.byref(ko))
     assert (ko.tol, ko.maxit, ko.restart, ko.max_restarts) == (1e-8, 10000, 30, 200)
     assert np.dtype(np.int32).itemsize == ctypes.sizeof(ctypes.c_int)
+    assert (opt.sf_gate_levels, opt.stage_min_rows, opt.stage_max_density,
+            opt.stage_position, opt.er_corner) == (-1, 0, 0.0, 0.0, 0)
+    # the C struct is no larger than the binding's: jv_default_options writes
+    # nothing past ctypes.sizeof (a canary after the struct survives)
+    size = ctypes.sizeof(_jv.jv_options)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    lib.jv_default_options(ctypes.byref(buf))
+    assert bytes(buf[size:]) == b"\xab" * 64
