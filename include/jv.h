@@ -139,6 +139,13 @@ typedef struct {
                                        the corner empty (jv_info.corner_rows = 0).  Not
                                        offered with band_rows > 0 (JV_ERR_ARG).  0 = off
                                        (default). */
+    int no_graphs;                  /* 1: issue the launch sequences of LEVEL and HYBRID (one
+                                       launch per upper-stage level) one by one.  0 (default):
+                                       the first call of a sequence captures it into a CUDA
+                                       graph, later calls with the same operation, dtypes,
+                                       buffers and mode replay it (up to 16 graphs per
+                                       handle; inside a stream capture of the caller's own
+                                       the launches go into that capture). */
 } jv_options;
 
 typedef struct {

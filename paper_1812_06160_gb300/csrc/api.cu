@@ -49,6 +49,7 @@ void destroy_handle(jv_handle h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     jv::free_workspace(h);
+    jv::free_graphs(h);
     jv::free_all(h);
     if (h->fscratch) cudaFree(h->fscratch);
     if (h->pscratch) cudaFree(h->pscratch);
@@ -93,6 +94,7 @@ void jv_default_options(jv_options *opt) {
     opt->stage_max_density = 0.0;
     opt->stage_position = 0.0;
     opt->er_corner = 0;
+    opt->no_graphs = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {

@@ -596,14 +596,17 @@ int run(jv_handle h, const void *vals, void *lu) {
             h->pscratch_bytes = need;
         }
     }
-    if (inplace) {
-        void *copy = static_cast<char *>(h->fscratch) + (size_t)h->nnz * sizeof(double);
-        JV_CUDA(cudaMemcpyAsync(copy, vals, (size_t)h->nnz * sizeof(TV), cudaMemcpyDeviceToDevice, s));
-        vals = copy;
-    }
-    if (h->opt.mode == JV_MODE_SYNCFREE && L.band.use)
+    const void *const user_vals = vals;
+    void *const copy = inplace ? static_cast<char *>(h->fscratch) + (size_t)h->nnz * sizeof(double)
+                               : nullptr;
+    if (inplace) vals = copy;
+    if (h->opt.mode == JV_MODE_SYNCFREE && L.band.use) {
+        if (inplace)
+            JV_CUDA(cudaMemcpyAsync(copy, user_vals, (size_t)h->nnz * sizeof(TV),
+                                    cudaMemcpyDeviceToDevice, s));
         return band_factor(h, sizeof(TV) == 8 ? JV_F64 : JV_F32, vals,
                            sizeof(TL) == 8 ? JV_F64 : JV_F32, lu, h->fscratch);
+    }
     FactorArgs a;
     a.rowptr = h->rowptr;
     a.diag = h->diag;
@@ -639,38 +642,49 @@ int run(jv_handle h, const void *vals, void *lu) {
     const jv_dtype lu_t = sizeof(TL) == 8 ? JV_F64 : JV_F32;
     const CornerPlan &C = h->corner[lu_t];
     const int lend = C.use ? C.K : L.nlev;
-    auto one_level = [&](int l) {
-        a.task_begin = W.h_task_ptr[l];
-        a.task_end = W.h_task_ptr[l + 1];
-        return launch<TV, TL, false>(W.window, h->fslot,
-                                     grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
-    };
-    auto sync_free = [&](int l0, int l1) {
-        a.task_begin = W.h_task_ptr[l0];
-        a.task_end = W.h_task_ptr[l1];
-        if (a.task_end <= a.task_begin) return (int)JV_OK;
-        return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, a.task_end - a.task_begin), s, a);
-    };
-    int rc = JV_OK;
-    if (h->opt.mode != JV_MODE_LEVEL) {
-        rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
-        if (rc) return rc;
-    }
-    if (h->opt.mode == JV_MODE_SYNCFREE) {
-        rc = sync_free(0, lend);
-    } else if (h->opt.mode == JV_MODE_LEVEL) {
-        for (int l = 0; l < lend && rc == JV_OK; ++l) rc = one_level(l);
-    } else {
-        for (const Seg &g : L.segs) {
-            if (g.l0 >= lend || rc != JV_OK) break;
-            const int l1 = std::min(g.l1, lend);
-            if (g.sf) rc = sync_free(g.l0, l1);
-            else for (int l = g.l0; l < l1 && rc == JV_OK; ++l) rc = one_level(l);
+    // the launch sequence on stream s (the handle's, or a capture stream)
+    auto seq = [&](cudaStream_t s) -> int {
+        if (inplace)
+            JV_CUDA(cudaMemcpyAsync(copy, user_vals, (size_t)h->nnz * sizeof(TV), cudaMemcpyDeviceToDevice, s));
+        auto one_level = [&](int l) {
+            a.task_begin = W.h_task_ptr[l];
+            a.task_end = W.h_task_ptr[l + 1];
+            return launch<TV, TL, false>(W.window, h->fslot,
+                                         grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+        };
+        auto sync_free = [&](int l0, int l1) {
+            a.task_begin = W.h_task_ptr[l0];
+            a.task_end = W.h_task_ptr[l1];
+            if (a.task_end <= a.task_begin) return (int)JV_OK;
+            return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, a.task_end - a.task_begin), s, a);
+        };
+        int rc = JV_OK;
+        if (h->opt.mode != JV_MODE_LEVEL) {
+            rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
+            if (rc) return rc;
         }
-    }
-    if (rc) return rc;
-    // the second stage: Even-Rows corner
-    return corner_factor(h, sizeof(TV) == 8 ? JV_F64 : JV_F32, vals, lu_t, lu);
+        if (h->opt.mode == JV_MODE_SYNCFREE) {
+            rc = sync_free(0, lend);
+        } else if (h->opt.mode == JV_MODE_LEVEL) {
+            for (int l = 0; l < lend && rc == JV_OK; ++l) rc = one_level(l);
+        } else {
+            for (const Seg &g : L.segs) {
+                if (g.l0 >= lend || rc != JV_OK) break;
+                const int l1 = std::min(g.l1, lend);
+                if (g.sf) rc = sync_free(g.l0, l1);
+                else for (int l = g.l0; l < l1 && rc == JV_OK; ++l) rc = one_level(l);
+            }
+        }
+        if (rc) return rc;
+        // the second stage: Even-Rows corner
+        return corner_factor(h, sizeof(TV) == 8 ? JV_F64 : JV_F32, vals, lu_t, lu, s);
+    };
+    if (h->opt.mode == JV_MODE_SYNCFREE) return seq(s);
+    const std::vector<unsigned long long> key = {
+        1, sizeof(TV), sizeof(TL), (unsigned long long)h->opt.mode, (unsigned long long)(uintptr_t)user_vals,
+        (unsigned long long)(uintptr_t)lu, (unsigned long long)(uintptr_t)h->fscratch,
+        (unsigned long long)(uintptr_t)h->pscratch};
+    return graph_run(h, key, seq);
 }
 
 }  // namespace

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <vector>
 
 #include "jv.h"
@@ -348,6 +349,15 @@ struct LevelSet {
 
 struct Workspace;  // Krylov scratch, krylov.cu
 
+// A captured launch sequence (graph.cu), keyed by operation, dtypes, buffers
+// and schedule.
+struct GraphEntry {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;   // kernels in the graph (launch counter)
+    unsigned long long used = 0;       // last use (least recently used goes first)
+};
+
 }  // namespace jv
 
 struct jv_handle_s {
@@ -392,6 +402,9 @@ struct jv_handle_s {
     int bad_row = -1;                        // row of the last analysis error
     int num_sms = 152;
     jv::Workspace *ws = nullptr;
+    std::vector<jv::GraphEntry> graphs;      // replayable per-level launch sequences
+    unsigned long long graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;       // private stream the sequences are captured on
     std::vector<void *> allocs;              // everything to cudaFree on destroy
 };
 
@@ -442,9 +455,16 @@ int band_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dty
 int band_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu,
                 void *scratch);
 
+// graph.cu: run seq(stream) through a cached CUDA graph of it (or plainly,
+// with no_graphs or inside a capture of the caller's own)
+int graph_run(jv_handle h, const std::vector<unsigned long long> &key,
+              const std::function<int(cudaStream_t)> &seq);
+void free_graphs(jv_handle h);
+
 // stages.cu: stage test, hybrid segments, Even-Rows corner
 int plan_stages(jv_handle h);
-int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu);
+int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu,
+                  cudaStream_t s);
 // launches of a hybrid run over levels [0, lend) of structure s (per-level tasks)
 int hybrid_launches(const LevelSet &L, int lend);
 

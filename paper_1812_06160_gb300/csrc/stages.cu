@@ -349,7 +349,8 @@ int hybrid_launches(const LevelSet &L, int lend) {
     return k;
 }
 
-int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu) {
+int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu,
+                  cudaStream_t s) {
     const CornerPlan &C = h->corner[lu_t];
     if (!C.use) return JV_OK;
     const size_t tl = lu_t == JV_F64 ? 8 : 4;
@@ -376,7 +377,6 @@ int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t,
     a.off_lptr = a.off_pptr + (int)up16((size_t)(C.R + 1) * 4);
     a.off_prog = a.off_lptr + (int)up16((size_t)(C.nl + 1) * 4);
     const int smem = a.off_prog + (int)up16((size_t)C.words * 2);
-    cudaStream_t s = h->stream;
 #define JV_CORNER(TV_, TL_)                                                                   \
     JV_CUDA(cudaFuncSetAttribute(k_er_corner<TV_, TL_>,                                        \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));          \

@@ -452,33 +452,42 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
         a.task_begin = multi ? L.h_ptr[l0] : W.h_task_ptr[l0];
         a.task_end = multi ? L.h_ptr[l1] : W.h_task_ptr[l1];
     };
-    auto one_level = [&](int l) {
-        tasks(l, l + 1);
-        return launch<TL, TB, TX, false>(multi, W.window,
-                                         grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
-    };
-    auto sync_free = [&](int l0, int l1) {
-        tasks(l0, l1);
-        if (a.task_end <= a.task_begin) return (int)JV_OK;
-        return launch<TL, TB, TX, true>(multi, W.window, sf_grid(h, a.task_end - a.task_begin), s, a);
-    };
-    int rc = JV_OK;
-    if (h->opt.mode != JV_MODE_LEVEL) {
-        rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
-        if (rc) return rc;
-    }
-    if (h->opt.mode == JV_MODE_SYNCFREE) return sync_free(0, L.nlev);
-    if (h->opt.mode == JV_MODE_LEVEL) {
-        for (int l = 0; l < L.nlev && rc == JV_OK; ++l) rc = one_level(l);
+    // the launch sequence on stream s (the handle's, or a capture stream)
+    auto seq = [&](cudaStream_t s) -> int {
+        auto one_level = [&](int l) {
+            tasks(l, l + 1);
+            return launch<TL, TB, TX, false>(multi, W.window,
+                                             grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
+        };
+        auto sync_free = [&](int l0, int l1) {
+            tasks(l0, l1);
+            if (a.task_end <= a.task_begin) return (int)JV_OK;
+            return launch<TL, TB, TX, true>(multi, W.window, sf_grid(h, a.task_end - a.task_begin), s, a);
+        };
+        int rc = JV_OK;
+        if (h->opt.mode != JV_MODE_LEVEL) {
+            rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
+            if (rc) return rc;
+        }
+        if (h->opt.mode == JV_MODE_SYNCFREE) return sync_free(0, L.nlev);
+        if (h->opt.mode == JV_MODE_LEVEL) {
+            for (int l = 0; l < L.nlev && rc == JV_OK; ++l) rc = one_level(l);
+            return rc;
+        }
+        // hybrid: upper-stage levels one launch each, second-stage runs sync-free
+        for (const Seg &g : L.segs) {
+            if (rc != JV_OK) break;
+            if (g.sf) rc = sync_free(g.l0, g.l1);
+            else for (int l = g.l0; l < g.l1 && rc == JV_OK; ++l) rc = one_level(l);
+        }
         return rc;
-    }
-    // hybrid: upper-stage levels one launch each, second-stage runs sync-free
-    for (const Seg &g : L.segs) {
-        if (rc != JV_OK) break;
-        if (g.sf) rc = sync_free(g.l0, g.l1);
-        else for (int l = g.l0; l < g.l1 && rc == JV_OK; ++l) rc = one_level(l);
-    }
-    return rc;
+    };
+    if (h->opt.mode == JV_MODE_SYNCFREE) return seq(s);
+    const std::vector<unsigned long long> key = {
+        2, (unsigned long long)structure, sizeof(TL), sizeof(TB), sizeof(TX),
+        (unsigned long long)h->opt.mode, (unsigned long long)(uintptr_t)lu,
+        (unsigned long long)(uintptr_t)b, (unsigned long long)(uintptr_t)x, (unsigned long long)nrhs};
+    return graph_run(h, key, seq);
 }
 
 }  // namespace
