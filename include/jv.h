@@ -57,10 +57,10 @@ typedef enum { JV_F64 = 0, JV_F32 = 1 } jv_dtype;
  * SYNCFREE: one launch; rows are claimed in level order and each waits only
  *           on its own dependencies (the point-to-point synchronisation of
  *           Sec. III-A, Fig. 4, with per-row flags in global memory).
- * HYBRID:   the two-stage split of Sec. III-A (Fig. 5): levels that pass the
+ * HYBRID:   the two-stage split of Sec. III-A (Fig. 2): levels that pass the
  *           stage test (stage_min_rows, stage_max_density, stage_position
  *           below) run one launch per level, and every maximal run of the
- *           other levels -- thin or dense levels between wide ones (Fig. 6)
+ *           other levels -- thin or dense levels between wide ones (Fig. 3)
  *           and the tail -- runs as one sync-free launch. */
 typedef enum { JV_MODE_LEVEL = 0, JV_MODE_SYNCFREE = 1, JV_MODE_HYBRID = 2 } jv_mode;
 

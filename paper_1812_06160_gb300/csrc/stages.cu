@@ -1,4 +1,4 @@
-// Two-stage schedules (Sec. III-A, Fig. 5): the stage test that splits the
+// Two-stage schedules (Sec. III-A, Fig. 2): the stage test that splits the
 // levels of every dependency structure into upper-stage levels and
 // second-stage material, the hybrid schedule built on it, and the Even-Rows
 // corner of the factor (Sec. III-B, Fig. 8) with its one-CTA kernel.

@@ -1,4 +1,4 @@
-"""Two-stage schedules (Sec. III-A, Fig. 5; Sec. III-B, Fig. 8) on the GPU.
+"""Two-stage schedules (Sec. III-A, Fig. 2; Sec. III-B, Fig. 8) on the GPU.
 
 Hybrid: the launch plan follows the stage test (rows per level, row density,
 relative position) worked out here from the oracle's level sets, and the
