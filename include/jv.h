@@ -136,9 +136,14 @@ typedef struct {
                                        exactly.  The corner's rows must be the last rows of
                                        the handle's order (reorder = 1 guarantees it; else
                                        JV_ERR_ARG); a tail too large for shared memory leaves
-                                       the corner empty (jv_info.corner_rows = 0).  Not
-                                       offered with band_rows > 0 (JV_ERR_ARG).  0 = off
-                                       (default). */
+                                       the corner empty (jv_info.corner_rows = 0).  The
+                                       one-column solves get corners of their own the same
+                                       way: the tail levels of each structure, when they are
+                                       the last rows (L, U^T) or the first rows (U, L^T),
+                                       solved by one CTA in shared memory after the upper
+                                       stage, with every row's sum in the serial order
+                                       (jv_info.solve_corner_rows).  Not offered with
+                                       band_rows > 0 (JV_ERR_ARG).  0 = off (default). */
     int no_graphs;                  /* 1: issue the launch sequences of LEVEL and HYBRID (one
                                        launch per upper-stage level) one by one.  0 (default):
                                        the first call of a sequence captures it into a CUDA
@@ -166,6 +171,8 @@ typedef struct {
     int corner_rows[2];         /* rows of the Even-Rows corner per factor jv_dtype (the
                                    FP32 corner holds about twice the rows); 0: none */
     int corner_levels[2];       /* levels of lower(A) each corner spans */
+    int solve_corner_rows[4][2];/* rows of the one-column solve corner per jv_structure;
+                                   [1]: factor and x both FP32, [0]: otherwise */
 } jv_info;
 
 /* Fill *opt with the defaults above. */

@@ -54,7 +54,8 @@ class jv_info(ctypes.Structure):
                 ("band_rows", ctypes.c_int * 4), ("nband_levels", ctypes.c_int * 4),
                 ("npairs", ctypes.c_longlong), ("mode", ctypes.c_int), ("reorder", ctypes.c_int),
                 ("hybrid_launches", ctypes.c_int * 4), ("hybrid_launches_factor", ctypes.c_int),
-                ("corner_rows", ctypes.c_int * 2), ("corner_levels", ctypes.c_int * 2)]
+                ("corner_rows", ctypes.c_int * 2), ("corner_levels", ctypes.c_int * 2),
+                ("solve_corner_rows", (ctypes.c_int * 2) * 4)]
 
 
 class jv_krylov_opts(ctypes.Structure):
@@ -355,7 +356,8 @@ def jv_get_info(h):
                 npairs=info.npairs, mode=info.mode, reorder=info.reorder,
                 hybrid_launches=list(info.hybrid_launches),
                 hybrid_launches_factor=info.hybrid_launches_factor,
-                corner_rows=list(info.corner_rows), corner_levels=list(info.corner_levels))
+                corner_rows=list(info.corner_rows), corner_levels=list(info.corner_levels),
+                solve_corner_rows=[list(r) for r in info.solve_corner_rows])
 
 
 def jv_get_levels(h, which="L"):

@@ -639,6 +639,7 @@ void free_all(jv_handle h) {
     for (auto &L : h->ls) L = LevelSet();
     h->fbins = Bins();
     for (auto &C : h->corner) C = CornerPlan();
+    for (auto &S : h->scorner) S[0] = S[1] = SolveCorner();
 }
 
 int analyze(jv_handle h, const int *rowptr, const int *colidx) {

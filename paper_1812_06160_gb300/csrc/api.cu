@@ -269,6 +269,8 @@ int jv_get_info(jv_handle h, jv_info *info) {
     for (int t = 0; t < 2; ++t) {
         info->corner_rows[t] = h->corner[t].use ? h->corner[t].R : 0;
         info->corner_levels[t] = h->corner[t].use ? h->corner[t].nl : 0;
+        for (int k = 0; k < 4; ++k)
+            info->solve_corner_rows[k][t] = h->scorner[k][t].use ? h->scorner[k][t].R : 0;
     }
     return JV_OK;
 }

@@ -659,7 +659,7 @@ int run(jv_handle h, const void *vals, void *lu) {
             return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, a.task_end - a.task_begin), s, a);
         };
         int rc = JV_OK;
-        if (h->opt.mode != JV_MODE_LEVEL) {
+        if (has_sync_free(h, L, lend)) {
             rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
             if (rc) return rc;
         }

@@ -316,6 +316,28 @@ struct CornerPlan {
 };
 constexpr int kCornerThreads = 1024;
 
+// Even-Rows corner of a single right-hand-side solve: the tail levels [K,
+// nlev) of the structure's DAG, whose rows are the last rows [c0, n) of a
+// forward structure (L, U^T) or the first rows [0, R) of a backward one (U,
+// L^T).  One CTA keeps the corner's x (and the operands it reads from rows
+// outside the corner, gathered once) in shared memory and solves the corner
+// level by level.  Per row (level order) the program holds [row - c0,
+// entries] and one operand slot per entry, in the serial order of the
+// substitution; the entry values (then the diagonal, for U and U^T) follow
+// the same order in a value array.
+struct SolveCorner {
+    bool use = false;
+    int K = 0, nl = 0;          // first level, levels
+    int c0 = 0, R = 0;          // first row, rows
+    int next = 0;               // operands outside the corner
+    int nval = 0, words = 0;    // values (entries + diagonals), program words
+    int *prog_ptr = nullptr;    // [R+1]
+    int *lvl_ptr = nullptr;     // [nl+1]
+    int *vpos = nullptr;        // [nval] position in lu of every value
+    int *ext = nullptr;         // [next] row of every outside operand
+    unsigned short *prog = nullptr;  // [words] (padded to an even count)
+};
+
 // Band schedule of one level structure: rows split into nb contiguous bands
 // of B rows (natural order); inside a band, rows are grouped by their local
 // level -- the longest path through dependencies that stay inside the band.
@@ -384,6 +406,7 @@ struct jv_handle_s {
     long long npairs = 0;
     jv::Bins fbins;                          // factor work list over the levels of lower(A)
     jv::CornerPlan corner[2];                // Even-Rows corner per factor dtype (jv_dtype)
+    jv::SolveCorner scorner[4][2];           // per structure; [1]: lu and x both FP32
     int maxrow = 0;                          // longest row
     // spmv row blocks: block b covers rows [spmv_blk[b], spmv_blk[b+1])
     int *spmv_blk = nullptr;
@@ -467,6 +490,13 @@ int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t,
                   cudaStream_t s);
 // launches of a hybrid run over levels [0, lend) of structure s (per-level tasks)
 int hybrid_launches(const LevelSet &L, int lend);
+// whether the handle's schedule runs a sync-free launch over levels [0, lend)
+// (which needs the output pre-filled with the sentinel)
+bool has_sync_free(jv_handle h, const LevelSet &L, int lend);
+// the solve corner a one-column solve of this structure and these value sizes uses, or null
+const SolveCorner *solve_corner_of(jv_handle h, int structure, size_t tl, size_t tx);
+int corner_solve(jv_handle h, int structure, const SolveCorner &C, jv_dtype lu_t, const void *lu,
+                 jv_dtype b_t, const void *b, jv_dtype x_t, void *x, cudaStream_t s);
 
 // trisolve.cu
 int hop_latency(int rounds, int npartners, double *out_us, cudaStream_t s);

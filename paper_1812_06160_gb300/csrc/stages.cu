@@ -19,6 +19,8 @@ namespace jv {
 
 namespace {
 
+size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 template <class T> struct RN;
 template <> struct RN<double> {
     __device__ static double fms(double a, double b, double c) { return __fma_rn(-a, b, c); }
@@ -188,7 +190,6 @@ int build_corner(jv_handle h, int K, size_t tl, CornerPlan &C) {
     pptr[R] = (int)prog.size();
     if (prog.size() & 1) prog.push_back(0);
     for (int l = K; l <= nlev; ++l) lptr[l - K] = L.h_ptr[l] - L.h_ptr[K];
-    auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     C.K = K;
     C.nl = nlev - K;
     C.c = c;
@@ -251,6 +252,41 @@ int plan_corner(jv_handle h) {
     return JV_OK;
 }
 
+// Staging loops of the one-CTA kernels: each thread keeps kStage loads in
+// flight (a plain strided loop would wait for each load before the next).
+constexpr int kStage = 8;
+template <class Load, class Store>
+__device__ __forceinline__ void stage(int count, Load load, Store store) {
+    using T = decltype(load(0));
+    const int nt = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < count; i0 += kStage * nt) {
+        T v[kStage];
+#pragma unroll
+        for (int k = 0; k < kStage; ++k)
+            if (i0 + k * nt < count) v[k] = load(i0 + k * nt);
+#pragma unroll
+        for (int k = 0; k < kStage; ++k)
+            if (i0 + k * nt < count) store(i0 + k * nt, v[k]);
+    }
+}
+// dst[i] = src[idx[i]]: the indices, then the values, kStage at a time
+template <class T>
+__device__ __forceinline__ void stage_gather(int count, const int *idx, const T *src, T *dst) {
+    const int nt = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < count; i0 += kStage * nt) {
+        int p[kStage];
+#pragma unroll
+        for (int k = 0; k < kStage; ++k) p[k] = i0 + k * nt < count ? __ldg(idx + i0 + k * nt) : -1;
+        T v[kStage];
+#pragma unroll
+        for (int k = 0; k < kStage; ++k)
+            if (p[k] >= 0) v[k] = src[p[k]];
+#pragma unroll
+        for (int k = 0; k < kStage; ++k)
+            if (p[k] >= 0) dst[i0 + k * nt] = v[k];
+    }
+}
+
 struct CornerArgs {
     const int *rowptr, *diag, *kdiag, *pair_ptr;
     const int2 *pairs;
@@ -278,13 +314,13 @@ __global__ void __launch_bounds__(kCornerThreads, 1) k_er_corner(CornerArgs a) {
     unsigned short *prog = reinterpret_cast<unsigned short *>(smem + a.off_prog);
     const int tid = threadIdx.x, nt = blockDim.x;
     const TV *vals = static_cast<const TV *>(a.vals) + a.E0;
-    for (int e = tid; e < a.E; e += nt) sv[e] = (TL)__ldg(vals + e);
-    for (int r = tid; r <= a.R; r += nt) pptr[r] = __ldg(a.prog_ptr + r);
-    for (int l = tid; l <= a.nl; l += nt) lptr[l] = __ldg(a.lvl_ptr + l);
+    stage(a.E, [&](int e) { return (TL)__ldg(vals + e); }, [&](int e, TL v) { sv[e] = v; });
+    stage(a.R + 1, [&](int r) { return __ldg(a.prog_ptr + r); }, [&](int r, int v) { pptr[r] = v; });
+    stage(a.nl + 1, [&](int l) { return __ldg(a.lvl_ptr + l); }, [&](int l, int v) { lptr[l] = v; });
     {
         const unsigned *src = reinterpret_cast<const unsigned *>(a.prog);
         unsigned *dst = reinterpret_cast<unsigned *>(prog);
-        for (int w = tid; w < (a.words >> 1); w += nt) dst[w] = __ldg(src + w);
+        stage(a.words >> 1, [&](int w) { return __ldg(src + w); }, [&](int w, unsigned v) { dst[w] = v; });
     }
     __syncthreads();
     const TL *lu = static_cast<const TL *>(a.lu);
@@ -330,13 +366,276 @@ __global__ void __launch_bounds__(kCornerThreads, 1) k_er_corner(CornerArgs a) {
     for (int e = tid; e < a.E; e += nt) out[e] = sv[e];
 }
 
+// Build the solve corner of structure s over its levels [K, nlev), if its
+// rows are the last rows (forward structures) or the first rows (backward
+// ones) of the handle's order and its slots fit 16 bits.  Leaves C unused
+// otherwise.
+int build_solve_corner(jv_handle h, int s, int K, SolveCorner &C) {
+    const LevelSet &L = h->ls[s];
+    const int n = h->n, nlev = L.nlev;
+    cudaStream_t st = h->stream;
+    C = SolveCorner();
+    const int R = n - L.h_ptr[K];
+    if (R <= 0) return JV_OK;
+    const bool forward = s == JV_LOWER || s == JV_UPPER_T;
+    const bool unit = s == JV_LOWER || s == JV_LOWER_T;
+    const bool reverse = s == JV_LOWER_T;
+    const bool csc = s == JV_UPPER_T || s == JV_LOWER_T;
+    const int c0 = forward ? n - R : 0, c1 = forward ? n : R;
+    std::vector<int> order(R);
+    JV_CUDA(cudaMemcpyAsync(order.data(), L.rows + L.h_ptr[K], (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+    // ptr[c0..c1], dg[c0..c1) of the CSR (L, U) or CSC (U^T, L^T); CSR diag for the pivots
+    std::vector<int> hptr(R + 1), hdg(R), hdiag(R);
+    JV_CUDA(cudaMemcpyAsync(hptr.data(), (csc ? h->colptr : h->rowptr) + c0, (size_t)(R + 1) * 4,
+                            cudaMemcpyDeviceToHost, st));
+    JV_CUDA(cudaMemcpyAsync(hdg.data(), (csc ? h->cdiag : h->diag) + c0, (size_t)R * 4,
+                            cudaMemcpyDeviceToHost, st));
+    JV_CUDA(cudaMemcpyAsync(hdiag.data(), h->diag + c0, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+    JV_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r)
+        if (order[r] < c0 || order[r] >= c1) return JV_OK;   // not a contiguous end: no corner
+    const int q0 = hptr[0], q1 = hptr[R];
+    std::vector<int> hidx(q1 - q0 + 1), hvmap(csc ? q1 - q0 + 1 : 1);
+    if (q1 > q0) {
+        JV_CUDA(cudaMemcpyAsync(hidx.data(), (csc ? h->rowidx : h->colidx) + q0, (size_t)(q1 - q0) * 4,
+                                cudaMemcpyDeviceToHost, st));
+        if (csc)
+            JV_CUDA(cudaMemcpyAsync(hvmap.data(), h->csc2csr + q0, (size_t)(q1 - q0) * 4,
+                                    cudaMemcpyDeviceToHost, st));
+        JV_CUDA(cudaStreamSynchronize(st));
+    }
+    std::vector<unsigned short> prog;
+    std::vector<int> pptr(R + 1), lptr(nlev - K + 1), vpos, ext;
+    std::vector<int> slot_of;                  // outside row -> slot, by binary search on ext
+    std::vector<std::pair<int, int>> pending;  // (row, program word) of outside operands
+    for (int r = 0; r < R; ++r) {
+        const int i = order[r], rl = i - c0;
+        int b, e;
+        switch (s) {                            // the substitution's dependency range
+            case JV_LOWER:   b = hptr[rl];        e = hdg[rl];          break;
+            case JV_UPPER:   b = hdg[rl] + 1;     e = hptr[rl + 1];     break;
+            case JV_UPPER_T: b = hptr[rl];        e = hdg[rl];          break;
+            default:         b = hdg[rl] + 1;     e = hptr[rl + 1];     break;
+        }
+        const int ne = e - b;
+        pptr[r] = (int)prog.size();
+        prog.push_back((unsigned short)rl);
+        prog.push_back((unsigned short)ne);
+        for (int k = 0; k < ne; ++k) {
+            const int q = reverse ? e - 1 - k : b + k;
+            const int j = hidx[q - q0];
+            if (j >= c0 && j < c1) {
+                prog.push_back((unsigned short)(j - c0));
+            } else {
+                pending.push_back({j, (int)prog.size()});
+                prog.push_back(0);
+            }
+            vpos.push_back(csc ? hvmap[q - q0] : q);
+        }
+        if (!unit) vpos.push_back(hdiag[rl]);
+    }
+    pptr[R] = (int)prog.size();
+    for (auto &pw : pending) ext.push_back(pw.first);
+    std::sort(ext.begin(), ext.end());
+    ext.erase(std::unique(ext.begin(), ext.end()), ext.end());
+    if ((long long)R + (long long)ext.size() >= 65536) return JV_OK;
+    for (auto &pw : pending) {
+        const int k = (int)(std::lower_bound(ext.begin(), ext.end(), pw.first) - ext.begin());
+        prog[pw.second] = (unsigned short)(R + k);
+    }
+    if (prog.size() & 1) prog.push_back(0);
+    for (int l = K; l <= nlev; ++l) lptr[l - K] = L.h_ptr[l] - L.h_ptr[K];
+    C.K = K;
+    C.nl = nlev - K;
+    C.c0 = c0;
+    C.R = R;
+    C.next = (int)ext.size();
+    C.nval = (int)vpos.size();
+    C.words = (int)prog.size();
+    JV_TRY(halloc_n(h, &C.prog_ptr, R + 1));
+    JV_TRY(halloc_n(h, &C.lvl_ptr, C.nl + 1));
+    JV_TRY(halloc_n(h, &C.vpos, vpos.size() + 1));
+    JV_TRY(halloc_n(h, &C.ext, ext.size() + 1));
+    JV_TRY(halloc_n(h, &C.prog, prog.size()));
+    JV_CUDA(cudaMemcpyAsync(C.prog_ptr, pptr.data(), (size_t)(R + 1) * 4, cudaMemcpyHostToDevice, st));
+    JV_CUDA(cudaMemcpyAsync(C.lvl_ptr, lptr.data(), (size_t)(C.nl + 1) * 4, cudaMemcpyHostToDevice, st));
+    if (!vpos.empty())
+        JV_CUDA(cudaMemcpyAsync(C.vpos, vpos.data(), vpos.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!ext.empty())
+        JV_CUDA(cudaMemcpyAsync(C.ext, ext.data(), ext.size() * 4, cudaMemcpyHostToDevice, st));
+    JV_CUDA(cudaMemcpyAsync(C.prog, prog.data(), prog.size() * 2, cudaMemcpyHostToDevice, st));
+    JV_CUDA(cudaStreamSynchronize(st));
+    C.use = true;
+    return JV_OK;
+}
+
+// Shared memory of a solve corner: x and outside operands, values, program,
+// row and level pointers.
+size_t solve_corner_smem(const SolveCorner &C, size_t tl, size_t tx) {
+    return up16((size_t)(C.R + C.next) * tx) + up16((size_t)C.nval * tl) + up16((size_t)C.words * 2) +
+           up16((size_t)(C.R + 1) * 4) + up16((size_t)(C.nl + 1) * 4);
+}
+
+// The solve corners of every structure for both value-size classes: the
+// tail of second-stage levels, shortened from its top until a bound on its
+// shared memory fits one CTA.
+int plan_solve_corners(jv_handle h) {
+    const int n = h->n;
+    int budget = 0;
+    JV_CUDA(cudaDeviceGetAttribute(&budget, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    for (int s = 0; s < 4; ++s) {
+        const LevelSet &L = h->ls[s];
+        const int nlev = L.nlev;
+        if (nlev == 0) continue;
+        Dev d;
+        unsigned long long *dsum;
+        JV_TRY(d.get(&dsum, nlev));
+        JV_CUDA(cudaMemsetAsync(dsum, 0, (size_t)nlev * 8, h->stream));
+        Span beg, end;
+        spans_of(h, s, &beg, &end);
+        count_launch();
+        k_level_len<<<grid_for(n, kBlock), kBlock, 0, h->stream>>>(n, beg, end, L.lev, dsum);
+        JV_CHECK_LAUNCH();
+        std::vector<unsigned long long> ent(nlev);
+        JV_CUDA(cudaMemcpyAsync(ent.data(), dsum, (size_t)nlev * 8, cudaMemcpyDeviceToHost, h->stream));
+        JV_CUDA(cudaStreamSynchronize(h->stream));
+        for (int k = 0; k < 2; ++k) {
+            const size_t tl = k == 0 ? 8 : 4, tx = tl;
+            unsigned long long E = 0;
+            int K = nlev;
+            while (K > L.tail) {
+                const unsigned long long E2 = E + ent[K - 1];
+                const unsigned long long R2 = (unsigned long long)(n - L.h_ptr[K - 1]);
+                const unsigned long long need = (R2 + E2) * tx + 16 + (E2 + R2) * tl + 16 +
+                                                (2 * R2 + E2 + 1) * 2 + 16 + (R2 + 1) * 4 + 16 +
+                                                (unsigned long long)(nlev - K + 2) * 4 + 16;
+                if (R2 + E2 >= 65536 || need > (unsigned long long)budget) break;
+                E = E2;
+                --K;
+            }
+            JV_TRY(build_solve_corner(h, s, K, h->scorner[s][k]));
+        }
+    }
+    return JV_OK;
+}
+
+struct SolveCornerArgs {
+    const int *prog_ptr, *lvl_ptr, *vpos, *ext;
+    const unsigned short *prog;
+    const void *lu, *b;
+    void *x;
+    int c0, R, next, nval, words, nl, unit;
+    int off_val, off_prog, off_pptr, off_lptr;
+};
+
+// One CTA: x of the corner rows (first b, cast as the substitution casts it)
+// and the outside operands in shared memory, with the values and programs;
+// then the corner's levels in order, separated by __syncthreads, one thread
+// per row: s = b_r; s = s - t_rj x_j in the serial order; x_r = s [/ u_rr].
+template <class TL, class TB, class TX>
+__global__ void __launch_bounds__(kCornerThreads, 1) k_trsv_corner(SolveCornerArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    TX *X = reinterpret_cast<TX *>(smem);
+    TL *val = reinterpret_cast<TL *>(smem + a.off_val);
+    unsigned short *prog = reinterpret_cast<unsigned short *>(smem + a.off_prog);
+    int *pptr = reinterpret_cast<int *>(smem + a.off_pptr);
+    int *lptr = reinterpret_cast<int *>(smem + a.off_lptr);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const TB *b = static_cast<const TB *>(a.b) + a.c0;
+    const TX *x = static_cast<const TX *>(a.x);
+    const TL *lu = static_cast<const TL *>(a.lu);
+    stage(a.R, [&](int l) { return (TX)(TL)b[l]; }, [&](int l, TX v) { X[l] = v; });
+    stage_gather(a.next, a.ext, x, X + a.R);
+    stage_gather(a.nval, a.vpos, lu, val);
+    stage(a.R + 1, [&](int r) { return __ldg(a.prog_ptr + r); }, [&](int r, int v) { pptr[r] = v; });
+    stage(a.nl + 1, [&](int l) { return __ldg(a.lvl_ptr + l); }, [&](int l, int v) { lptr[l] = v; });
+    {
+        const unsigned *src = reinterpret_cast<const unsigned *>(a.prog);
+        unsigned *dst = reinterpret_cast<unsigned *>(prog);
+        stage(a.words >> 1, [&](int w) { return __ldg(src + w); }, [&](int w, unsigned v) { dst[w] = v; });
+    }
+    __syncthreads();
+    for (int l = 0; l < a.nl; ++l) {
+        const int r1 = lptr[l + 1];
+        for (int r = lptr[l] + tid; r < r1; r += nt) {
+            const int w = pptr[r];
+            const int rl = prog[w], ne = prog[w + 1];
+            const int vb = w - 2 * r + (a.unit ? 0 : r);
+            TL s = (TL)X[rl];
+            for (int e = 0; e < ne; ++e) s = RN<TL>::fms(val[vb + e], (TL)X[prog[w + 2 + e]], s);
+            if (!a.unit) s = RN<TL>::div(s, val[vb + ne]);
+            X[rl] = (TX)s;
+        }
+        __syncthreads();
+    }
+    TX *out = static_cast<TX *>(a.x) + a.c0;
+    for (int l = tid; l < a.R; l += nt) out[l] = X[l];
+}
+
 }  // namespace
 
 int plan_stages(jv_handle h) {
     for (int s = 0; s < 4; ++s) JV_TRY(stage_test(h, s));
     for (auto &C : h->corner) C = CornerPlan();
-    if (h->opt.er_corner) JV_TRY(plan_corner(h));
+    for (auto &S : h->scorner) S[0] = S[1] = SolveCorner();
+    if (h->opt.er_corner) {
+        JV_TRY(plan_corner(h));
+        JV_TRY(plan_solve_corners(h));
+    }
     return JV_OK;
+}
+
+const SolveCorner *solve_corner_of(jv_handle h, int structure, size_t tl, size_t tx) {
+    const SolveCorner &C = h->scorner[structure][tl == 4 && tx == 4 ? 1 : 0];
+    return C.use ? &C : nullptr;
+}
+
+int corner_solve(jv_handle h, int structure, const SolveCorner &C, jv_dtype lu_t, const void *lu,
+                 jv_dtype b_t, const void *b, jv_dtype x_t, void *x, cudaStream_t s) {
+    const size_t tl = lu_t == JV_F64 ? 8 : 4, tx = x_t == JV_F64 ? 8 : 4;
+    SolveCornerArgs a{};
+    a.prog_ptr = C.prog_ptr;
+    a.lvl_ptr = C.lvl_ptr;
+    a.vpos = C.vpos;
+    a.ext = C.ext;
+    a.prog = C.prog;
+    a.lu = lu;
+    a.b = b;
+    a.x = x;
+    a.c0 = C.c0;
+    a.R = C.R;
+    a.next = C.next;
+    a.nval = C.nval;
+    a.words = C.words;
+    a.nl = C.nl;
+    a.unit = structure == JV_LOWER || structure == JV_LOWER_T;
+    a.off_val = (int)up16((size_t)(C.R + C.next) * tx);
+    a.off_prog = a.off_val + (int)up16((size_t)C.nval * tl);
+    a.off_pptr = a.off_prog + (int)up16((size_t)C.words * 2);
+    a.off_lptr = a.off_pptr + (int)up16((size_t)(C.R + 1) * 4);
+    const int smem = (int)solve_corner_smem(C, tl, tx);
+#define JV_SCORNER(TL_, TB_, TX_)                                                            \
+    JV_CUDA(cudaFuncSetAttribute(k_trsv_corner<TL_, TB_, TX_>,                                \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));         \
+    count_launch();                                                                          \
+    k_trsv_corner<TL_, TB_, TX_><<<1, kCornerThreads, smem, s>>>(a);
+    if (lu_t == JV_F64 && b_t == JV_F64 && x_t == JV_F64) { JV_SCORNER(double, double, double) }
+    else if (lu_t == JV_F32 && b_t == JV_F32 && x_t == JV_F32) { JV_SCORNER(float, float, float) }
+    else if (lu_t == JV_F32 && b_t == JV_F64 && x_t == JV_F32) { JV_SCORNER(float, double, float) }
+    else if (lu_t == JV_F32 && b_t == JV_F32 && x_t == JV_F64) { JV_SCORNER(float, float, double) }
+    else if (lu_t == JV_F32 && b_t == JV_F64 && x_t == JV_F64) { JV_SCORNER(float, double, double) }
+    else return JV_ERR_ARG;
+#undef JV_SCORNER
+    JV_CHECK_LAUNCH();
+    return JV_OK;
+}
+
+bool has_sync_free(jv_handle h, const LevelSet &L, int lend) {
+    if (lend <= 0 || h->opt.mode == JV_MODE_LEVEL) return false;
+    if (h->opt.mode == JV_MODE_SYNCFREE) return true;
+    for (const Seg &g : L.segs)
+        if (g.l0 < lend && g.sf) return true;
+    return false;
 }
 
 int hybrid_launches(const LevelSet &L, int lend) {
@@ -354,7 +653,6 @@ int corner_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t,
     const CornerPlan &C = h->corner[lu_t];
     if (!C.use) return JV_OK;
     const size_t tl = lu_t == JV_F64 ? 8 : 4;
-    auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     CornerArgs a{};
     a.rowptr = h->rowptr;
     a.diag = h->diag;

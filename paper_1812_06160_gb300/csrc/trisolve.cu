@@ -28,6 +28,8 @@
 // over all levels (see sf_next_chunk); the output vector is pre-filled with a
 // sentinel bit pattern and one relaxed store publishes a finished value, so
 // each dependency is awaited on its own output word (no flags, no fences).
+#include <algorithm>
+
 #include "jv_internal.cuh"
 
 namespace jv {
@@ -447,6 +449,10 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
     a.backoff_ns = sf_backoff(h);
+    // a one-column solve may end in an Even-Rows corner: the upper stage
+    // then runs the levels above it
+    const SolveCorner *C = multi ? nullptr : solve_corner_of(h, structure, sizeof(TL), sizeof(TX));
+    const int lend = C ? C->K : L.nlev;
     // tasks of levels [l0, l1): rows (several right-hand sides) or work-list tasks
     auto tasks = [&](int l0, int l1) {
         a.task_begin = multi ? L.h_ptr[l0] : W.h_task_ptr[l0];
@@ -465,22 +471,25 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
             return launch<TL, TB, TX, true>(multi, W.window, sf_grid(h, a.task_end - a.task_begin), s, a);
         };
         int rc = JV_OK;
-        if (h->opt.mode != JV_MODE_LEVEL) {
+        if (has_sync_free(h, L, lend)) {
             rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
             if (rc) return rc;
         }
-        if (h->opt.mode == JV_MODE_SYNCFREE) return sync_free(0, L.nlev);
-        if (h->opt.mode == JV_MODE_LEVEL) {
-            for (int l = 0; l < L.nlev && rc == JV_OK; ++l) rc = one_level(l);
-            return rc;
+        if (h->opt.mode == JV_MODE_SYNCFREE) {
+            rc = sync_free(0, lend);
+        } else if (h->opt.mode == JV_MODE_LEVEL) {
+            for (int l = 0; l < lend && rc == JV_OK; ++l) rc = one_level(l);
+        } else {
+            // hybrid: upper-stage levels one launch each, second-stage runs sync-free
+            for (const Seg &g : L.segs) {
+                if (g.l0 >= lend || rc != JV_OK) break;
+                const int l1 = std::min(g.l1, lend);
+                if (g.sf) rc = sync_free(g.l0, l1);
+                else for (int l = g.l0; l < l1 && rc == JV_OK; ++l) rc = one_level(l);
+            }
         }
-        // hybrid: upper-stage levels one launch each, second-stage runs sync-free
-        for (const Seg &g : L.segs) {
-            if (rc != JV_OK) break;
-            if (g.sf) rc = sync_free(g.l0, g.l1);
-            else for (int l = g.l0; l < g.l1 && rc == JV_OK; ++l) rc = one_level(l);
-        }
-        return rc;
+        if (rc != JV_OK || !C) return rc;
+        return corner_solve(h, structure, *C, dt<TL>(), lu, dt<TB>(), b, dt<TX>(), x, s);
     };
     if (h->opt.mode == JV_MODE_SYNCFREE) return seq(s);
     const std::vector<unsigned long long> key = {

@@ -254,3 +254,65 @@ def test_hybrid_full_size_c2():
     assert np.array_equal(y.cpu().numpy(), O.lsolve(rp, ci, diag, olu, b))
     z = jv.jv_usolve(h, lu, y)
     assert np.array_equal(z.cpu().numpy(), O.usolve(rp, ci, diag, olu, y.cpu().numpy()))
+
+
+SOLVES = (("L", 0, "jv_lsolve", O.lsolve), ("U", 1, "jv_usolve", O.usolve),
+          ("Ut", 2, "jv_usolve_t", O.usolve_t), ("Lt", 3, "jv_lsolve_t", O.lsolve_t))
+
+
+def check_solve_corners(rp, ci, v, brp, bci, olu, mode, min_rows, seed):
+    """The four one-column solves with corners: FP64 bit-exact with the
+    oracle; FP32 (every mix of b and x precisions) bit-exact with the
+    sync-free path without corners."""
+    n = len(brp) - 1
+    h = jv.jv_analyze(T(rp), T(ci), reorder=True, er_corner=True, mode=mode,
+                      stage_min_rows=min_rows)
+    h0 = jv.jv_analyze(T(rp), T(ci), reorder=True)
+    info = jv.jv_get_info(h)
+    diag = O.diag_ptr(brp, bci)
+    b = W.rhs(n, 1, seed=seed)
+    lu = T(olu)
+    for _, k, fn, ofn in SOLVES:
+        got = getattr(jv, fn)(h, lu, T(b)).cpu().numpy()
+        assert np.array_equal(got, ofn(brp, bci, diag, olu, b)), (fn, info["solve_corner_rows"][k])
+    lu32 = lu.float()
+    for bt in (torch.float32, torch.float64):
+        for xt in (torch.float32, torch.float64):
+            bb = T(b).to(bt)
+            for _, _, fn, _ in SOLVES:
+                x1 = getattr(jv, fn)(h, lu32, bb, x_dtype=xt)
+                x0 = getattr(jv, fn)(h0, lu32, bb, x_dtype=xt)
+                assert x1.dtype == xt and torch.equal(x1, x0), (fn, bt, xt)
+    # several columns: no corner, the plain schedule
+    B3 = W.rhs(n, 3, seed=seed + 1)
+    assert np.array_equal(jv.jv_usolve(h, lu, T(B3)).cpu().numpy(),
+                          O.usolve(brp, bci, diag, olu, B3))
+    return info
+
+
+@pytest.mark.parametrize("mode", ["syncfree", "level", "hybrid"])
+@pytest.mark.parametrize("min_rows", [0, 6])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_er_solve_corners_bit_exact(case, min_rows, mode):
+    name, rp, ci, v = case
+    brp, bci, bv = reordered(rp, ci, v)
+    olu, st, _ = O.ilu0(brp, bci, bv)
+    if st != O.OK:
+        pytest.skip("zero pivot case")
+    info = check_solve_corners(rp, ci, v, brp, bci, olu, mode, min_rows, seed=31)
+    if min_rows == 0 and name not in ("powerlaw6000", "rand1"):
+        assert info["solve_corner_rows"][0][0] > 0 and info["solve_corner_rows"][0][1] > 0
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c5"])
+def test_er_solve_corners_full_size(cfg):
+    c = W.config(cfg)
+    rp, ci, v = c["rowptr"], c["colidx"], c["vals"]
+    brp, bci, bv = reordered(rp, ci, v)
+    olu, st, _ = O.ilu0(brp, bci, bv)
+    assert st == O.OK
+    info = check_solve_corners(rp, ci, v, brp, bci, olu, "syncfree", 0, seed=41)
+    # symmetric patterns in level order: every structure's tail is an end of the order
+    assert all(r[0] > 0 and r[1] >= r[0] for r in info["solve_corner_rows"])
+    if cfg == "c1":                                   # the whole FP32 solve fits one CTA
+        assert all(r[1] == len(rp) - 1 for r in info["solve_corner_rows"])
