@@ -243,10 +243,19 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                     seen |= 1u << k;
                     V(len + k) = B::from(u[k]);
                 }
-            if (!done && seen == need) {
+            const bool ready = !done && seen == need;
+            bool go = ready;
+            if constexpr (sizeof(TL) == 8) {
+                // FP64: every warp instruction of the finish (divisions and
+                // fused multiply-adds) costs the same with 1 or 32 lanes, so
+                // the rows wait until all rows of the warp are ready and
+                // finish together (C2 factor 1.50 -> 1.29 ms, C5 3.94 -> 3.72)
+                if (!__all_sync(0xffffffffu, done || ready)) go = false;
+            }
+            if (go) {
                 finish();
                 done = true;
-            } else if (!done) {
+            } else if (!done && !ready) {
                 if (rounds++ == 0) t0 = clock64();
                 if ((rounds & 15u) == 0) {
                     if (sf_aborted(a.ticket)) {
