@@ -54,7 +54,9 @@ KERNEL_SOURCES = {"factor": ("factor.cu", "jv_internal.cuh"),
                   "lsolve": ("trisolve.cu", "jv_internal.cuh"),
                   "usolve": ("trisolve.cu", "jv_internal.cuh")}
 TRAFFIC = {
-    ("c2", "f64", "factor", "syncfree", False): (537_024_768, "6e3032055783"),
+    ("c2", "f64", "factor", "syncfree", False): (536_797_440, "bc187b2eefd4"),
+    ("c2", "f64", "lsolve", "syncfree", False): (251_881_472, "33e3a03f5dbe"),
+    ("c2", "f64", "usolve", "syncfree", False): (253_885_952, "33e3a03f5dbe"),
 }
 
 

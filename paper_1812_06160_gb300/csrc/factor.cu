@@ -272,31 +272,40 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     }
     int wb = 0, wend = 0;
     while (__any_sync(0xffffffffu, !done)) {
-        if (done) continue;
-        if (got == wend) {              // next window of operands [wb, wend)
-            wb = got;
-            wend = min(got + W, m);
-        }
-        // (re-)read every operand of the window not taken yet; they tend to be
-        // published together, so they are all polled in the same round
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-            if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(lu + OPOS(wb + k));
-        bool ok = true;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            if (wb + k < got) continue;
-            if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
-                V(len + wb + k) = B::from(u[k]);
-                ++got;
-            } else {
-                ok = false;
+        bool ready = false;
+        if (!done) {
+            if (got == wend) {              // next window of operands [wb, wend)
+                wb = got;
+                wend = min(got + W, m);
             }
+            // (re-)read every operand of the window not taken yet; they tend to be
+            // published together, so they are all polled in the same round
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(lu + OPOS(wb + k));
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (wb + k < got) continue;
+                if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
+                    V(len + wb + k) = B::from(u[k]);
+                    ++got;
+                } else {
+                    ok = false;
+                }
+            }
+            ready = got == m;
         }
-        if (got == m) {
+        bool go = ready;
+        if constexpr (sizeof(TL) == 8) {
+            // FP64: finish the warp's rows together, as in the single-window
+            // loop (C2 MILU(0) factor 3.12 -> 2.21 ms)
+            if (!__all_sync(0xffffffffu, done || ready)) go = false;
+        }
+        if (go) {
             finish();
             done = true;
-        } else if (SF && got < wend) {
+        } else if (SF && !done && !ready && got < wend) {
             if (rounds++ == 0) t0 = clock64();
             if ((rounds & 15u) == 0) {
                 if (sf_aborted(a.ticket)) {
