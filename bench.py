@@ -370,42 +370,46 @@ def main(argv=None):
     lu = torch.empty_like(vals)
     y = torch.empty_like(rhs)
     z = torch.empty_like(rhs)
+    # one set of step buffers: the inputs the e2e run copies in, the outputs it
+    # copies back, and the intermediates (shared by the sets: the kernels run
+    # in order on one stream)
     if meta["adjoint"]:
         gy = torch.empty_like(rhs)
-        gr = torch.empty_like(rhs)
-        glu = torch.zeros_like(vals)
-        outputs = [gr, glu]
-        inputs = [vals, rhs, g_in]
+        B0 = {"lu": lu, "y": y, "z": z, "gy": gy, "vals": vals, "rhs": rhs, "g_in": g_in,
+              "gr": torch.empty_like(rhs), "glu": torch.zeros_like(vals)}
+        in_names, out_names = ["vals", "rhs", "g_in"], ["gr", "glu"]
     else:
-        s = torch.empty(n, dtype=dt, device=dev)
-        outputs = [z, s]
-        inputs = [vals, rhs]
+        B0 = {"lu": lu, "y": y, "vals": vals, "rhs": rhs, "z": z,
+              "s": torch.empty(n, dtype=dt, device=dev)}
+        in_names, out_names = ["vals", "rhs"], ["z", "s"]
+    inputs = [B0[k] for k in in_names]
+    outputs = [B0[k] for k in out_names]
 
-    def run_kernel(k):
+    def run_kernel(k, B=B0):
         if k == "factor":
-            jv.jv_ilu0_factor(h, vals, lu)
+            jv.jv_ilu0_factor(h, B["vals"], B["lu"])
         elif k == "lsolve":
-            jv.jv_lsolve(h, lu, rhs, y)
+            jv.jv_lsolve(h, B["lu"], B["rhs"], B["y"])
         elif k == "usolve":
-            jv.jv_usolve(h, lu, y, z)
+            jv.jv_usolve(h, B["lu"], B["y"], B["z"])
         elif k == "spmv":
-            jv.jv_spmv(h, vals, z, s)
+            jv.jv_spmv(h, B["vals"], B["z"], B["s"])
         elif k == "usolve_t":
-            jv.jv_usolve_t(h, lu, g_in, gy)
+            jv.jv_usolve_t(h, B["lu"], B["g_in"], B["gy"])
         elif k == "lsolve_t":
-            jv.jv_lsolve_t(h, lu, gy, gr)
+            jv.jv_lsolve_t(h, B["lu"], B["gy"], B["gr"])
         else:  # outer
-            jv.jv_masked_outer(h, 0, gr, y, alpha=-1.0, g=glu)
-            jv.jv_masked_outer(h, 1, gy, z, alpha=-1.0, g=glu)
+            jv.jv_masked_outer(h, 0, B["gr"], B["y"], alpha=-1.0, g=B["glu"])
+            jv.jv_masked_outer(h, 1, B["gy"], B["z"], alpha=-1.0, g=B["glu"])
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(ev=None):
+    def step(ev=None, B=B0):
         for i, k in enumerate(kernels):
             if ev is not None:
                 ev[i].record(stream)
-            run_kernel(k)
+            run_kernel(k, B)
         if ev is not None:
             ev[len(kernels)].record(stream)
 
@@ -482,22 +486,72 @@ def main(argv=None):
             for hdst, d in zip(host_out, outputs):
                 hdst.copy_(d, non_blocking=True)
 
-        for _ in range(max(2, a.warmup // 2)):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        def timed(fn, k2):
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            barrier(world)
+            e0.record(stream)
+            fn(k2)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            check_status()
+            return reduce_max(e0.elapsed_time(e1) / k2, world)
+
+        # serial: every step copies its inputs in, runs, copies its results out
+        def serial(k2):
+            for _ in range(k2):
+                e2e_step()
+
+        # pipelined: while step i runs, the copy engines bring step i+1's inputs
+        # in and take step i-1's results out (two input and output buffer sets;
+        # every step still copies all of its inputs and results)
+        B1 = dict(B0)
+        for k in in_names + out_names:
+            B1[k] = torch.empty_like(B0[k])
+        sets = [B0, B1]
+        cs_in, cs_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+        def pipelined(k2):
+            ev = lambda: torch.cuda.Event()
+            in_ready, done, out_done = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+            start = ev()
+            start.record(stream)
+
+            def copy_in(i):
+                with torch.cuda.stream(cs_in):
+                    cs_in.wait_event(start)
+                    if i >= 2:
+                        cs_in.wait_event(done[i % 2])     # step i-2 has read this set
+                    for name, hsrc in zip(in_names, host_in):
+                        sets[i % 2][name].copy_(hsrc, non_blocking=True)
+                    in_ready[i % 2].record(cs_in)
+
+            copy_in(0)
+            for i in range(k2):
+                if i + 1 < k2:
+                    copy_in(i + 1)
+                stream.wait_event(in_ready[i % 2])
+                if i >= 2:
+                    stream.wait_event(out_done[i % 2])     # step i-2's results are out
+                step(B=sets[i % 2])
+                done[i % 2].record(stream)
+                with torch.cuda.stream(cs_out):
+                    cs_out.wait_event(done[i % 2])
+                    for hdst, name in zip(host_out, out_names):
+                        hdst.copy_(sets[i % 2][name], non_blocking=True)
+                    out_done[i % 2].record(cs_out)
+            stream.wait_event(out_done[(k2 - 1) % 2])
+
         k2 = max(3, a.steps // 2)
-        barrier(world)
-        e0.record(stream)
-        for _ in range(k2):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        check_status()
-        e2e_ms = reduce_max(e0.elapsed_time(e1) / k2, world)
+        serial(max(2, a.warmup // 2))
+        serial_ms = timed(serial, k2)
+        pipelined(max(2, a.warmup // 2))
+        e2e_ms = timed(pipelined, k2)
         line["e2e"] = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
-                       "ms_per_step": e2e_ms,
+                       "ms_per_step": e2e_ms, "pipelined": True,
+                       "serial": {"value": world * step_bytes / (serial_ms * 1e-3) / 1e9,
+                                  "ms_per_step": serial_ms},
                        "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in host_in),
                        "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in host_out)}
 
