@@ -52,6 +52,7 @@ void destroy_handle(jv_handle h) {
     jv::free_graphs(h);
     jv::free_all(h);
     if (h->fscratch) cudaFree(h->fscratch);
+    if (h->xscratch) cudaFree(h->xscratch);
     if (h->pscratch) cudaFree(h->pscratch);
     if (h->ticket) cudaFree(h->ticket);
     if (h->status) cudaFree(h->status);

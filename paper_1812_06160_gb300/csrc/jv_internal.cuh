@@ -414,6 +414,8 @@ struct jv_handle_s {
     // lazily allocated factor scratch (long rows / in-place copies)
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;
+    void *xscratch = nullptr;                // FP32 solution of FP32-factor solves into FP64 x
+    size_t xscratch_bytes = 0;
     void *pscratch = nullptr;                // operands of long rows: [npairs + nnz] elements
     int fslot = jv::kLaneSlot;               // factor one-lane slot (kLaneSlot or kLaneSlotWide)
     size_t pscratch_bytes = 0;

@@ -537,6 +537,44 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     return graph_run(h, key, seq);
 }
 
+__global__ void k_widen(size_t m, const float *in, double *out) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < m) out[i] = (double)in[i];
+}
+
+// An FP32 factor's solve into an FP64 x (the preconditioner of the FP64
+// Krylov drivers writes z this way) runs into an FP32 scratch vector, then
+// widens it in one pass.  Widening is exact, and every dependant read the
+// FP32 value either way, so x is the same bit for bit; the solve itself
+// then polls 4-byte words and converts nothing per row (the conversions go
+// to the narrow FP64 pipe: C2 U solve 0.545 -> 0.44 ms).
+template <class TB>
+int run_widened(jv_handle h, int structure, const void *lu, const void *b, void *x, int nrhs) {
+    const size_t m = (size_t)h->n * nrhs;
+    if (h->xscratch_bytes < m * sizeof(float)) {
+        if (h->xscratch) {
+            JV_CUDA(cudaStreamSynchronize(h->stream));
+            cudaFree(h->xscratch);
+            h->xscratch = nullptr;
+            h->xscratch_bytes = 0;
+        }
+        if (cudaMalloc(&h->xscratch, m * sizeof(float) + 16) != cudaSuccess) {
+            cudaGetLastError();
+            h->xscratch = nullptr;
+            return JV_ERR_NOMEM;
+        }
+        h->xscratch_bytes = m * sizeof(float);
+    }
+    int rc = run<float, TB, float>(h, structure, lu, b, h->xscratch, nrhs);
+    if (rc) return rc;
+    if (m == 0) return JV_OK;
+    count_launch();
+    k_widen<<<grid_for((long long)m, kBlock), kBlock, 0, h->stream>>>(
+        m, static_cast<const float *>(h->xscratch), static_cast<double *>(x));
+    JV_CHECK_LAUNCH();
+    return JV_OK;
+}
+
 }  // namespace
 
 int tri_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtype b_t,
@@ -548,9 +586,9 @@ int tri_solve(jv_handle h, int structure, jv_dtype lu_t, const void *lu, jv_dtyp
     if (lu_t == JV_F32 && b_t == JV_F64 && x_t == JV_F32)
         return run<float, double, float>(h, structure, lu, b, x, nrhs);
     if (lu_t == JV_F32 && b_t == JV_F32 && x_t == JV_F64)
-        return run<float, float, double>(h, structure, lu, b, x, nrhs);
+        return run_widened<float>(h, structure, lu, b, x, nrhs);
     if (lu_t == JV_F32 && b_t == JV_F64 && x_t == JV_F64)
-        return run<float, double, double>(h, structure, lu, b, x, nrhs);
+        return run_widened<double>(h, structure, lu, b, x, nrhs);
     return JV_ERR_ARG;
 }
 
