@@ -86,7 +86,8 @@ typedef struct {
                                        its dependants time out.  -1 (default) = off. */
     int sf_ctas_per_sm;             /* sync-free launches run a persistent grid of this many
                                        CTAs per SM (bounds how many rows poll at once);
-                                       0 = default */
+                                       0 = default (1; 2 for solves with several
+                                       right-hand sides, whose tasks are single rows) */
     int sf_backoff_ns;              /* longest pause between two polls of a value that is not
                                        ready; 0 = default, negative = never pause */
     int band_rows;                  /* sync-free band schedule: rows per band (> 0), one CTA

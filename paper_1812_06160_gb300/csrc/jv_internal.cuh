@@ -437,8 +437,8 @@ namespace jv {
 
 // Persistent grid of a sync-free launch over `ntasks` tasks, and the poll
 // back-off bound, from the handle's options.
-inline int sf_grid(jv_handle h, int ntasks) {
-    const int per_sm = h->opt.sf_ctas_per_sm > 0 ? h->opt.sf_ctas_per_sm : 1;
+inline int sf_grid(jv_handle h, int ntasks, int default_per_sm = 1) {
+    const int per_sm = h->opt.sf_ctas_per_sm > 0 ? h->opt.sf_ctas_per_sm : default_per_sm;
     const int chunks = (ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int g = h->num_sms * per_sm;
     return chunks < g ? (chunks > 0 ? chunks : 1) : g;
