@@ -111,13 +111,20 @@ def test_spmv(case):
     assert np.all(np.abs(y32 - O.spmv(rp, ci, v, x)) <= 1e-5 * (scale + 1e-30))
 
 
-@pytest.mark.parametrize("case", CASES[2:6], ids=IDS[2:6])
-def test_masked_outer(case):
+OUTER_CASES = [c for c in CASES if c[0] in ("rand37", "rand250", "rand600", "rand1500", "lap5_33",
+                                            "aniso5_41", "powerlaw6000", "band20_800")]
+
+
+@pytest.mark.parametrize("nrhs", [1, 7, 32])
+@pytest.mark.parametrize("case", OUTER_CASES, ids=[c[0] for c in OUTER_CASES])
+def test_masked_outer(case, nrhs):
+    # rows of at most 64 entries take the thread-per-row kernel, longer
+    # ones (powerlaw6000) the warp-per-row kernel
     _, rp, ci, _ = case
     n = len(rp) - 1
     h = jv.jv_analyze(T(rp), T(ci))
     diag = O.diag_ptr(rp, ci)
-    a, b = W.rhs(n, 7, seed=1), W.rhs(n, 7, seed=2)
+    a, b = W.rhs(n, nrhs, seed=1), W.rhs(n, nrhs, seed=2)
     for which in (0, 1):
         g = jv.jv_masked_outer(h, which, T(a), T(b), alpha=-1.0).cpu().numpy()
         want = O.masked_outer(rp, ci, diag, which, a, b, alpha=-1.0)
