@@ -54,9 +54,9 @@ KERNEL_SOURCES = {"factor": ("factor.cu", "jv_internal.cuh"),
                   "lsolve": ("trisolve.cu", "jv_internal.cuh"),
                   "usolve": ("trisolve.cu", "jv_internal.cuh")}
 TRAFFIC = {
-    ("c2", "f64", "factor", "syncfree", False): (536_797_440, "bc187b2eefd4"),
-    ("c2", "f64", "lsolve", "syncfree", False): (251_881_472, "33e3a03f5dbe"),
-    ("c2", "f64", "usolve", "syncfree", False): (253_885_952, "33e3a03f5dbe"),
+    ("c2", "f64", "factor", "syncfree", False): (537_112_832, "fe727fecab13"),
+    ("c2", "f64", "lsolve", "syncfree", False): (252_362_752, "df9c463a9e01"),
+    ("c2", "f64", "usolve", "syncfree", False): (253_896_960, "df9c463a9e01"),
 }
 
 
