@@ -2,6 +2,8 @@
 // repeats; Sec. VI defers it), the pattern-restricted outer product used by
 // the factor gradient, and the gathers that move values and vectors into the
 // level order of a reordered handle (Sec. III).
+#include <cstdint>
+
 #include "jv_internal.cuh"
 
 namespace jv {
@@ -77,9 +79,25 @@ __global__ void __launch_bounds__(kBlock) k_spmv(const int *__restrict__ blk,
     }
 }
 
+// 16-byte vector of T: four floats or two doubles
+template <class T> struct Vec16;
+template <> struct Vec16<float> {
+    using V = float4;
+    static constexpr int k = 4;
+    __device__ static float at(const V &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+};
+template <> struct Vec16<double> {
+    using V = double2;
+    static constexpr int k = 2;
+    __device__ static double at(const V &v, int e) { return e == 0 ? v.x : v.y; }
+};
+
 // g[p] = alpha * sum_c a[i,c] b[j,c] over the entries p = (i, j) of one part of
-// row i: one warp per row, one lane per entry, the sum over c in order.
-template <class T>
+// row i: one warp per row, one lane per entry, the sum over c in order.  VEC:
+// the rows of a and b are 16-byte aligned and a whole number of 16-byte
+// vectors long, so each lane reads them 16 bytes at a time (the kernel is
+// bound by load instructions); the fused multiply-adds keep the order c.
+template <class T, bool VEC>
 __global__ void __launch_bounds__(kBlock) k_masked_outer(int n, const int *rowptr, const int *colidx,
                                                          const int *diag, int which, const T *A,
                                                          const T *B, int nrhs, T alpha, T *g) {
@@ -93,7 +111,18 @@ __global__ void __launch_bounds__(kBlock) k_masked_outer(int n, const int *rowpt
     for (int p = lo + lane; p < hi; p += 32) {
         const T *bj = B + (size_t)__ldg(colidx + p) * ld;
         T s = 0;
-        for (int c = 0; c < nrhs; ++c) s = RN<T>::fma(__ldg(ai + c), __ldg(bj + c), s);
+        if constexpr (VEC) {
+            using W = Vec16<T>;
+            const typename W::V *a4 = reinterpret_cast<const typename W::V *>(ai);
+            const typename W::V *b4 = reinterpret_cast<const typename W::V *>(bj);
+            for (int c = 0; c < nrhs / W::k; ++c) {
+                const typename W::V x = __ldg(a4 + c), y = __ldg(b4 + c);
+#pragma unroll
+                for (int e = 0; e < W::k; ++e) s = RN<T>::fma(W::at(x, e), W::at(y, e), s);
+            }
+        } else {
+            for (int c = 0; c < nrhs; ++c) s = RN<T>::fma(__ldg(ai + c), __ldg(bj + c), s);
+        }
         g[p] = RN<T>::mul(alpha, s);
     }
 }
@@ -137,15 +166,19 @@ int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, doub
 int masked_outer(jv_handle h, jv_dtype t, int which, const void *a, const void *b, int nrhs,
                  double alpha, void *g) {
     const int grid = grid_for(h->n, kWarpsPerBlock);
+    const size_t row_bytes = (size_t)nrhs * (t == JV_F64 ? 8 : 4);
+    const bool vec = row_bytes % 16 == 0 && (uintptr_t)a % 16 == 0 && (uintptr_t)b % 16 == 0;
     count_launch();
-    if (t == JV_F64)
-        k_masked_outer<double><<<grid, kBlock, 0, h->stream>>>(
-            h->n, h->rowptr, h->colidx, h->diag, which, (const double *)a, (const double *)b, nrhs,
-            alpha, (double *)g);
-    else
-        k_masked_outer<float><<<grid, kBlock, 0, h->stream>>>(
-            h->n, h->rowptr, h->colidx, h->diag, which, (const float *)a, (const float *)b, nrhs,
-            (float)alpha, (float *)g);
+#define JV_OUTER(T_, V_)                                                                         \
+    k_masked_outer<T_, V_><<<grid, kBlock, 0, h->stream>>>(h->n, h->rowptr, h->colidx, h->diag,  \
+                                                           which, (const T_ *)a, (const T_ *)b,  \
+                                                           nrhs, (T_)alpha, (T_ *)g);
+    if (t == JV_F64) {
+        if (vec) { JV_OUTER(double, true) } else { JV_OUTER(double, false) }
+    } else {
+        if (vec) { JV_OUTER(float, true) } else { JV_OUTER(float, false) }
+    }
+#undef JV_OUTER
     JV_CHECK_LAUNCH();
     return JV_OK;
 }

@@ -129,6 +129,18 @@ def test_masked_outer(case, nrhs):
         g = jv.jv_masked_outer(h, which, T(a), T(b), alpha=-1.0).cpu().numpy()
         want = O.masked_outer(rp, ci, diag, which, a, b, alpha=-1.0)
         assert np.array_equal(g, want)
+        # FP32, and the 16-byte vector loads (aligned rows of 32 columns)
+        # against the scalar loads of the same data read from a copy that is
+        # 4 bytes off the 16-byte boundary
+        a32, b32 = T(a).float(), T(b).float()
+        g32 = jv.jv_masked_outer(h, which, a32, b32, alpha=-1.0)
+        buf_a = torch.empty(a32.numel() + 1, dtype=torch.float32, device="cuda")
+        buf_b = torch.empty(b32.numel() + 1, dtype=torch.float32, device="cuda")
+        ua, ub = buf_a[1:].view_as(a32), buf_b[1:].view_as(b32)
+        ua.copy_(a32)
+        ub.copy_(b32)
+        assert ua.data_ptr() % 16 != 0
+        assert torch.equal(jv.jv_masked_outer(h, which, ua, ub, alpha=-1.0), g32)
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
