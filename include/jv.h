@@ -179,6 +179,23 @@ typedef struct {
 /* Fill *opt with the defaults above. */
 void jv_default_options(jv_options *opt);
 
+/* The stage test of the two-stage schedules (Sec. III-A), on the host: what
+ * jv_analyze applies to each level structure, exported so that a caller can
+ * preview the split.  Nothing here touches a GPU.
+ * nlev: levels.  level_ptr[nlev+1] (host): the first position of every level
+ * in level order (level_ptr[0] = 0, strictly increasing, level_ptr[nlev] =
+ * n).  dep_sum[nlev] (host): the sum of the dependency counts of each
+ * level's rows, or NULL (then opt->stage_max_density must be 0).  opt: the
+ * stage_min_rows / stage_max_density / stage_position options, NULL for the
+ * defaults.  Writes upper[nlev] (host): 1 for an upper-stage level, 0 for
+ * second-stage material, and *tail (may be NULL): the first level of the run
+ * of second-stage levels that ends the structure (nlev if there is none).
+ * The hybrid schedule launches each upper-stage level on its own and each
+ * maximal run of other levels as one sync-free launch; the Even-Rows corner
+ * lies within [tail, nlev).  Returns JV_OK or JV_ERR_ARG. */
+int jv_stage_plan(int nlev, const int *level_ptr, const long long *dep_sum, int n,
+                  const jv_options *opt, unsigned char *upper, int *tail);
+
 /* Dependency analysis (Sec. II level scheduling; Sec. III-A upper stage).
  * n, nnz: matrix order and stored entries.  rowptr[n+1], colidx[nnz]: device
  * CSR pattern (values are not needed).  opt: host pointer or NULL for the

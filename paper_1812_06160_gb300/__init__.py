@@ -18,7 +18,7 @@ _BINDING = ("JV_OK", "JV_ERR_ARG", "JV_ERR_PATTERN", "JV_ERR_NO_DIAG", "JV_ERR_Z
             "jv_permute_vector", "jv_get_info", "jv_get_levels", "jv_get_pattern", "jv_get_csc",
             "jv_get_perm", "jv_status_sync", "jv_pcg", "jv_fgmres", "jv_launch_count",
             "jv_status_string", "jv_lsolve_noalloc", "jv_hop_latency",
-            "jv_iluk_symbolic", "jv_scatter_values")
+            "jv_iluk_symbolic", "jv_scatter_values", "jv_stage_plan")
 __all__ = list(_BINDING) + ["IluApply", "ilu_apply"]
 
 

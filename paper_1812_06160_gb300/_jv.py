@@ -79,6 +79,7 @@ _pi = ctypes.POINTER(ctypes.c_int)
 _pp = ctypes.POINTER(ctypes.c_void_p)
 _SIGS = {
     "jv_default_options": (None, [ctypes.POINTER(jv_options)]),
+    "jv_stage_plan": (_i, [_i, _v, _v, _i, ctypes.POINTER(jv_options), _v, ctypes.POINTER(_i)]),
     "jv_default_krylov_opts": (None, [ctypes.POINTER(jv_krylov_opts)]),
     "jv_analyze": (_i, [_i, _i, _v, _v, ctypes.POINTER(jv_options), _v, _pp]),
     "jv_last_bad_row": (_i, []),
@@ -238,6 +239,27 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
                             ctypes.byref(out))
     _check("jv_analyze", st, lib.jv_last_bad_row())
     return Handle(out.value, n, nnz, rowptr.device)
+
+
+def jv_stage_plan(level_ptr, dep_sum=None, stage_min_rows=0, stage_max_density=0.0,
+                  stage_position=0.0):
+    """The stage test on the host (no GPU): level_ptr[nlev+1] and optional
+    per-level dependency sums (numpy).  Returns (upper[nlev] as uint8, tail)."""
+    import numpy as np
+    lp = np.ascontiguousarray(level_ptr, dtype=np.int32)
+    nlev = len(lp) - 1
+    ds = None if dep_sum is None else np.ascontiguousarray(dep_sum, dtype=np.int64)
+    opt = jv_options()
+    lib.jv_default_options(ctypes.byref(opt))
+    opt.stage_min_rows = int(stage_min_rows)
+    opt.stage_max_density = float(stage_max_density)
+    opt.stage_position = float(stage_position)
+    upper = np.zeros(max(nlev, 1), dtype=np.uint8)
+    tail = ctypes.c_int(-1)
+    _check("jv_stage_plan", lib.jv_stage_plan(
+        nlev, lp.ctypes.data, None if ds is None else ds.ctypes.data, int(lp[-1]),
+        ctypes.byref(opt), upper.ctypes.data, ctypes.byref(tail)))
+    return upper[:nlev], tail.value
 
 
 def jv_destroy(h: Handle):

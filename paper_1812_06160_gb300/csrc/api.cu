@@ -2,11 +2,14 @@
 // handle's life cycle and the status protocol.  All arithmetic is in the
 // kernels of the other translation units.
 #include <cstring>
+#include <vector>
 
 #include "jv_internal.cuh"
 
 namespace jv {
 void free_all(jv_handle h);
+int stage_upper(int nlev, const int *level_ptr, const unsigned long long *len, int n,
+                const jv_options &opt, unsigned char *upper);
 }
 
 namespace {
@@ -243,6 +246,33 @@ int jv_permute_vector(jv_handle h, jv_dtype t, int inverse, const void *in, void
     if (rc) return rc;
     if (!h->perm || !in || !out || in == out || nrhs < 1 || !dtype_size(t)) return JV_ERR_ARG;
     return finish(h, jv::permute_vector(h, t, inverse ? 1 : 0, in, out, nrhs));
+}
+
+int jv_stage_plan(int nlev, const int *level_ptr, const long long *dep_sum, int n,
+                  const jv_options *opt, unsigned char *upper, int *tail) {
+    if (nlev < 0 || n < 0 || !level_ptr || (nlev > 0 && !upper)) return JV_ERR_ARG;
+    jv_options o;
+    if (opt) o = *opt; else jv_default_options(&o);
+    if (o.stage_min_rows < 0 || !(o.stage_max_density >= 0) || !(o.stage_position >= 0) ||
+        o.stage_position > 1)
+        return JV_ERR_ARG;
+    if (level_ptr[0] != 0) return JV_ERR_ARG;
+    for (int l = 0; l < nlev; ++l)
+        if (level_ptr[l + 1] <= level_ptr[l]) return JV_ERR_ARG;   // levels are never empty
+    if (level_ptr[nlev] != n) return JV_ERR_ARG;
+    std::vector<unsigned long long> len;
+    if (dep_sum) {
+        len.resize(nlev);
+        for (int l = 0; l < nlev; ++l) {
+            if (dep_sum[l] < 0) return JV_ERR_ARG;
+            len[l] = (unsigned long long)dep_sum[l];
+        }
+    } else if (o.stage_max_density > 0) {
+        return JV_ERR_ARG;
+    }
+    const int t = jv::stage_upper(nlev, level_ptr, dep_sum ? len.data() : nullptr, n, o, upper);
+    if (tail) *tail = t;
+    return JV_OK;
 }
 
 int jv_get_info(jv_handle h, jv_info *info) {

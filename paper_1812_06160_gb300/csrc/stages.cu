@@ -77,6 +77,36 @@ struct Dev {
     }
 };
 
+}  // namespace
+
+// The stage test of Sec. III-A on the host: upper[l] = 1 when level l has at
+// least stage_min_rows rows, a mean dependency count at most
+// stage_max_density times the structure's mean (len = per-level sums; the
+// mean is their total over n), and its first row before stage_position * n.
+// Returns the first level of the tail of second-stage levels.
+int stage_upper(int nlev, const int *level_ptr, const unsigned long long *len, int n,
+                const jv_options &opt, unsigned char *upper) {
+    unsigned long long total = 0;
+    if (len)
+        for (int l = 0; l < nlev; ++l) total += len[l];
+    const double mean = n > 0 ? (double)total / n : 0.0;
+    const int min_rows = opt.stage_min_rows > 0 ? opt.stage_min_rows : 1024;
+    const double pos = opt.stage_position;
+    for (int l = 0; l < nlev; ++l) {
+        const int w = level_ptr[l + 1] - level_ptr[l];
+        bool up = w >= min_rows;
+        if (up && opt.stage_max_density > 0 && len)
+            up = (double)len[l] / w <= opt.stage_max_density * mean;
+        if (up && pos > 0 && pos < 1) up = (double)level_ptr[l] < pos * n;
+        upper[l] = up ? 1 : 0;
+    }
+    int t = nlev;
+    while (t > 0 && !upper[t - 1]) --t;
+    return t;
+}
+
+namespace {
+
 // The stage test of Sec. III-A on every level of structure s: at least
 // stage_min_rows rows, mean dependency count at most stage_max_density times
 // the structure's mean, first row before stage_position * n.  Fills the
@@ -101,20 +131,8 @@ int stage_test(jv_handle h, int s) {
         JV_CUDA(cudaMemcpyAsync(len.data(), dsum, (size_t)nlev * 8, cudaMemcpyDeviceToHost, h->stream));
         JV_CUDA(cudaStreamSynchronize(h->stream));
     }
-    unsigned long long total = 0;
-    for (unsigned long long v : len) total += v;
-    const double mean = n > 0 ? (double)total / n : 0.0;
-    const int min_rows = h->opt.stage_min_rows > 0 ? h->opt.stage_min_rows : 1024;
-    const double pos = h->opt.stage_position;
-    std::vector<char> upper(nlev);
-    for (int l = 0; l < nlev; ++l) {
-        const int w = L.h_ptr[l + 1] - L.h_ptr[l];
-        bool up = w >= min_rows;
-        if (up && h->opt.stage_max_density > 0)
-            up = (double)len[l] / w <= h->opt.stage_max_density * mean;
-        if (up && pos > 0 && pos < 1) up = (double)L.h_ptr[l] < pos * n;
-        upper[l] = up;
-    }
+    std::vector<unsigned char> upper(nlev);
+    L.tail = stage_upper(nlev, L.h_ptr.data(), len.data(), n, h->opt, upper.data());
     for (int l = 0; l < nlev;) {
         if (upper[l]) {
             L.segs.push_back({l, l + 1, false});
@@ -126,9 +144,6 @@ int stage_test(jv_handle h, int s) {
             l = e;
         }
     }
-    int t = nlev;
-    while (t > 0 && !upper[t - 1]) --t;
-    L.tail = t;
     return JV_OK;
 }
 
