@@ -224,13 +224,11 @@ __device__ void iluk_row_paths(const IlukArgs &a, int i, int *sm, int *ovf) {
     int *kb = sm + 2 * kPathSlots, *vb = sm + 3 * kPathSlots;  // layer L + 1
     int *kf = sm + 4 * kPathSlots, *vf = sm + 5 * kPathSlots;  // result: level of fill
     __shared__ int s_cnt[kPathWarps];
-    __shared__ int s_bad[kPathWarps];
     const int wib = threadIdx.x >> 5;
     for (int t = lane; t < kPathSlots; t += 32) {
         ka[t] = -1; va[t] = 0x7fffffff;
         kf[t] = -1; vf[t] = 0x7fffffff;
     }
-    if (lane == 0) s_bad[wib] = 0;
     __syncwarp();
     bool bad = false;
     const int rs = __ldg(a.rowptr + i), re = __ldg(a.rowptr + i + 1);
