@@ -334,27 +334,32 @@ int jv_fgmres(jv_handle h, const double *vals, jv_dtype lu_t, const void *lu,
  * code with no place to keep a jv_handle).  Same arithmetic and result as
  * jv_lsolve with FP64 factor and vectors and one right-hand side.
  *   n <= 2097152 (2^21) rows, else JV_ERR_ARG (the scratch is fixed-size).
- *   rowptr[n+1], colidx[], diag[n]: CSR pattern of the factor and the
- *   position of every diagonal entry (e.g. from jv_get_pattern); lu[]: the
- *   factor from jv_ilu0_factor; order[n]: the rows in an order in which every
- *   row comes after all rows it depends on (the level sets of jv_get_levels
- *   for JV_LOWER, or simply 0..n-1); b[n] in, x[n] out (x must not alias b).
- *   stream: cudaStream_t (NULL = legacy default stream).  Synchronises the
- *   stream and returns JV_OK or JV_ERR_TIMEOUT (a wait gave up: order is not
- *   dependency-respecting).
+ *   rowptr[n+1], colidx[], diag[n]: a valid CSR pattern of the factor and the
+ *   position of every diagonal entry (e.g. from jv_get_pattern; they are
+ *   trusted); lu[]: the factor from jv_ilu0_factor; order[n]: the rows in an
+ *   order in which every row comes after all rows it depends on (the level
+ *   sets of jv_get_levels for JV_LOWER, or simply 0..n-1); b[n] in, x[n] out
+ *   (x must not alias b).  stream: cudaStream_t (NULL = legacy default
+ *   stream).
+ * Synchronous: waits for its own work on the stream and returns JV_OK,
+ * JV_ERR_ARG (also when an entry of order lies outside [0, n) or a strictly
+ * lower entry of a row names a column outside [0, row): such a row writes
+ * nothing) or JV_ERR_TIMEOUT (a wait gave up: order is not
+ * dependency-respecting -- a bad order may time out, or may still finish if
+ * the rows it waits on happen to be processed first).  After a failed call x
+ * is unspecified.
  * Its scratch (8 MB of per-row flags plus a few words) is one file-scope
  * device array that every GPU loading the library holds until the process
- * exits.  Its device address is looked up on the first call made on each
- * device, so make that first call before any stream capture.  All calls share
- * the array and each call clears it before use, so calls that overlap on the
- * GPU race. */
+ * exits; each call looks its device address up with the caller's device
+ * current.  All calls share the array and each call clears it before use, so
+ * calls that overlap on the GPU race. */
 int jv_lsolve_noalloc(int n, const int *rowptr, const int *colidx, const int *diag,
                       const int *order, const double *lu, const double *b, double *x,
                       void *stream);
 
 /* ILU(k) symbolic factorisation (the level-of-fill pattern that ILU(k)
- * factors on: Javelin runs its up-looking numeric sweep on the pattern "with
- * desired fill-in", Sec. II / Sec. V).  Entry (i, j) is kept when its level
+ * factors on: Javelin runs its up-looking numeric sweep on A's pattern
+ * widened by the requested fill, Sec. II / Sec. V).  Entry (i, j) is kept when its level
  * of fill is <= level, where every entry of A has level 0 and, row by row,
  * lev(i,j) = min over the columns k < i of row i (ascending, fill included)
  * of lev(i,k) + lev(k,j) + 1, for j in row k's filled pattern.  ILU(k) is

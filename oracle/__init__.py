@@ -5,8 +5,11 @@ CPU-baseline / reference leg of ``bench.py`` may import this package.  The
 product path (``paper_1812_06160_gb300``) never imports it and shares no code
 with it.
 
-The arithmetic lives in ``jv_oracle.c`` (plain C, compiled with
-``-ffp-contract=off`` so every multiply and subtract rounds separately); this
+The arithmetic lives in ``jv_oracle.c`` (plain C).  Every update
+``s <- s -/+ a*b`` there is one explicit fused multiply-add (C99 ``fma`` /
+``fmaf``: the product is not rounded on its own); every division and every
+other operation rounds separately, and the file is compiled with
+``-ffp-contract=off`` so that the compiler fuses nothing else.  This
 module compiles it on first use with the system C compiler and exposes numpy
 wrappers.  Each wrapper names the paper passage its C function follows.
 

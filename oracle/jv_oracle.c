@@ -356,9 +356,9 @@ int jvo_milu0_f32(int n, const int *rowptr, const int *colidx, const int *diag,
 
 /* ------------------------------------------------------------------------ */
 /* ILU(k) symbolic factorisation -- the level-of-fill pattern that ILU(k)     */
-/* factors on (Sec. II, and Sec. V "Incomplete levels": Javelin takes the     */
-/* pattern "with desired fill-in" and runs the same up-looking numeric sweep  */
-/* on it).  Row by row, i ascending: lev(i,j) = 0 for every entry of A's row  */
+/* factors on (Sec. II, and Sec. V "Incomplete levels": Javelin runs the     */
+/* same up-looking numeric sweep on a pattern widened by the fill the user    */
+/* asks for).  Row by row, i ascending: lev(i,j) = 0 for every entry of A's row  */
 /* i, otherwise unset; then for every column k < i of the row, in ascending   */
 /* order (fill columns included as they appear): for every column j > k of   */
 /* row k's filled pattern, lev(i,j) <- min(lev(i,j), lev(i,k) + lev(k,j) + 1) */

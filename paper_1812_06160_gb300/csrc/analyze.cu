@@ -260,7 +260,7 @@ int peel_levels(jv_handle h, const Dag &g, int *lev, Temp &tmp, int *nlev_out,
     widths.clear();
     int hs[kPeelBatch + 1];
     long long total = 0;
-    const int grid = 152 * 8;
+    const int grid = h->num_sms * 8;
     for (int level = 0;; level += kPeelBatch) {
         JV_CUDA(cudaMemsetAsync(sizes + 1, 0, kPeelBatch * sizeof(int), s));
         for (int b = 0; b < kPeelBatch; ++b) {

@@ -371,7 +371,7 @@ struct Dev {                                   // device allocations of one call
 int iluk_symbolic(int n, int nnz, const int *rowptr, const int *colidx, int level, int *fill_rowptr,
                   int *fill_colidx, int *fill_level, long long *fill_nnz, cudaStream_t s,
                   int *bad_row) {
-    int dev = 0, nsm = 152;
+    int dev = 0, nsm = 0;
     JV_CUDA(cudaGetDevice(&dev));
     JV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     Dev d;

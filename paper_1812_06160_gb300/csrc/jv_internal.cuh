@@ -454,6 +454,8 @@ template <class T> int halloc_n(jv_handle h, T **p, size_t count) {
 }
 
 // prims.cu
+// multiprocessors of the current device (queried once per device)
+int current_device_sms();
 int fill_u32(void *p, size_t count_u32, unsigned v, cudaStream_t s);
 int iota_i32(int *p, int n, cudaStream_t s);
 // exclusive scan of in[0..m) into out[0..m]; out[m] = total.  tmp: >= scan_tmp_ints(m)

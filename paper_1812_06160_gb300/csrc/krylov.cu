@@ -1,5 +1,5 @@
 // Krylov drivers (Sec. I: CG and GMRES preconditioned by the ILU factors;
-// the solves "may be called thousands of times", Sec. VI).  All vectors are
+// Sec. VI notes that the solves run many times over for one factor).  All vectors are
 // FP64 on the device; the scalars of the recurrences (alpha, beta, the
 // Hessenberg column) are produced and consumed on the device, and only one
 // residual norm (PCG) or one Hessenberg column (FGMRES, for the Givens

@@ -12,21 +12,22 @@
 // until the process exits (every GPU that loads the library holds it).
 //
 // Host code cannot use the array's name as a device address (in host code
-// it names a host-side stand-in): the device address is obtained once per
-// device with cudaGetSymbolAddress, with that device current, on the first
-// call made on it, and cached.  That first call must therefore come before any
-// stream capture.  All calls share the one array, which keeps what the last
-// call left in it: each call clears the words that must start at zero before
-// it uses them, and calls that overlap on the GPU (two streams, two threads)
-// race on the array.
+// it names a host-side stand-in): every call looks the device address up
+// with cudaGetSymbolAddress, with the caller's device current, so that a new
+// context on that device (after cudaDeviceReset, say) is never handed the
+// address of the old one.  All calls share the one array, which keeps what
+// the last call left in it: each call clears the words that must start at
+// zero before it uses them, and calls that overlap on the GPU (two streams,
+// two threads) race on the array.  The call is synchronous: it waits for its
+// own work to finish and reads the status word back.
 //
 // The schedule is a persistent sync-free sweep: CTAs claim chunks of
 // kWarpsPerBlock rows of the caller's row order, one warp per row; a row waits
 // (bounded) on an acquire-load of the ready flag of every row it reads, then
 // replays the ordered chain s = fma(-l_rj, x_j, s) in ascending column order
-// -- the serial forward substitution, so the result equals jv_lsolve's.
-#include <mutex>
-
+// -- the serial forward substitution.  A row whose wait gave up, or that
+// names a row or column outside the matrix, stores nothing and raises no
+// flag.
 #include "jv_internal.cuh"
 
 namespace jv {
@@ -41,22 +42,11 @@ constexpr size_t kNoAllocBytes = kNoAllocHeader + sizeof(int) * (size_t)kNoAlloc
 constexpr size_t kStatusOffset = 16;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array in the current device's context.
 int scratch_address(unsigned char **out) {
-    int dev = 0;
-    JV_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return JV_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        JV_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    JV_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<unsigned char *>(p);
     return JV_OK;
 }
 
@@ -89,27 +79,47 @@ __global__ void __launch_bounds__(kBlock) k_lsolve_noalloc(int n, const int *row
         const int t = base + wib;
         if (t >= n) continue;
         const int r = __ldg(order + t);
+        if ((unsigned)r >= (unsigned)n) {              // not a row of the matrix
+            if (lane == 0) {
+                report(status, JV_ERR_ARG, t);
+                sf_abort(ticket);
+            }
+            continue;
+        }
         const int q0 = __ldg(rowptr + r), q1 = __ldg(diag + r);
         double s = __ldg(b + r);
+        bool fail = false;                             // this lane gave up or saw a bad column
         for (int c0 = q0; c0 < q1; c0 += kWarp) {
             const int q = c0 + lane;
             double v = 0.0, xv = 0.0;
             if (q < q1) {
                 const int j = __ldg(colidx + q);
-                v = __ldg(lu + q);
-                if (ld_acquire_s32(flags + j) == 0) {
-                    const long long t0 = clock64();
-                    unsigned it = 0;
-                    while (ld_acquire_s32(flags + j) == 0) {
-                        if ((++it & 15u) == 0 &&
-                            (sf_aborted(ticket) || clock64() - t0 > timeout)) {
-                            report(status, JV_ERR_TIMEOUT, r);
-                            sf_abort(ticket);
-                            break;
+                if ((unsigned)j >= (unsigned)r) {     // not a strictly lower column of row r
+                    report(status, JV_ERR_ARG, r);
+                    sf_abort(ticket);
+                    fail = true;
+                } else {
+                    v = __ldg(lu + q);
+                    if (ld_acquire_s32(flags + j) == 0) {
+                        const long long t0 = clock64();
+                        unsigned it = 0;
+                        while (ld_acquire_s32(flags + j) == 0) {
+                            if ((++it & 15u) == 0) {
+                                if (sf_aborted(ticket)) {        // another wait gave up
+                                    fail = true;
+                                    break;
+                                }
+                                if (clock64() - t0 > timeout) {
+                                    report(status, JV_ERR_TIMEOUT, r);
+                                    sf_abort(ticket);
+                                    fail = true;
+                                    break;
+                                }
+                            }
                         }
                     }
+                    if (!fail) xv = ld_relaxed_f64(x + j);
                 }
-                xv = ld_relaxed_f64(x + j);
             }
             const int cnt = min(kWarp, q1 - c0);
             for (int l = 0; l < cnt; ++l) {
@@ -118,7 +128,8 @@ __global__ void __launch_bounds__(kBlock) k_lsolve_noalloc(int n, const int *row
                 s = __fma_rn(-vl, xl, s);
             }
         }
-        if (lane == 0) {
+        // a row that lacks an operand publishes neither its value nor its flag
+        if (!__any_sync(0xffffffffu, fail) && lane == 0) {
             x[r] = s;
             __threadfence();
             st_release(flags + r, 1);
@@ -146,7 +157,7 @@ extern "C" int jv_lsolve_noalloc(int n, const int *rowptr, const int *colidx, co
     int rc = scratch_address(&scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int sms = 152;
+    int sms = 0;
     int dev = 0;
     JV_CUDA(cudaGetDevice(&dev));
     JV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

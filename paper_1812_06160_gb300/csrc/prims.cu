@@ -3,6 +3,8 @@
 // All are deterministic: integer results do not depend on scheduling, and the
 // sort is stable (equal keys keep their input order), which is what makes the
 // level sets and the CSC bit-exact run to run.
+#include <mutex>
+
 #include "jv_internal.cuh"
 
 namespace jv {
@@ -24,11 +26,30 @@ __global__ void k_fill_u32(unsigned *p, size_t n, unsigned v) {
     for (size_t j = head + nv * 4 + i; j < n; j += stride) p[j] = v;
 }
 
+int current_device_sms() {
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            return 1;
+        }
+        cache[dev] = sms;
+    }
+    return cache[dev];
+}
+
 int fill_u32(void *p, size_t count, unsigned v, cudaStream_t s) {
     if (count == 0) return JV_OK;
     long long vec = (long long)(count / 4 + 1);
     int grid = grid_for(vec, kBlock);
-    if (grid > 152 * 16) grid = 152 * 16;
+    const int cap = current_device_sms() * 16;   // 16 CTAs per SM, grid-stride beyond
+    if (grid > cap) grid = cap;
     count_launch();
     k_fill_u32<<<grid, kBlock, 0, s>>>((unsigned *)p, count, v);
     JV_CHECK_LAUNCH();

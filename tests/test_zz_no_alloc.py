@@ -57,3 +57,42 @@ def test_noalloc_rejects_too_many_rows():
                                       small.data_ptr(), vec.data_ptr(), vec.data_ptr(),
                                       vec.data_ptr() + 8, None)
     assert st == jv.JV_ERR_ARG
+
+
+def test_noalloc_bad_order_times_out_then_recovers():
+    # reversed rows: every claimed chunk waits on rows that come later in the
+    # order; 13,824 rows make 1,728 chunks, more than the SMs can hold at once,
+    # so no schedule can finish them -- one bounded wait (about 2 s) expires,
+    # the call reports JV_ERR_TIMEOUT, and the next call starts clean
+    rp, ci, v = W.lap7(24)
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci))
+    lu = jv.jv_ilu0_factor(h, T(v))
+    rowptr, colidx, diag = jv.jv_get_pattern(h)
+    b = T(W.rhs(n, 1, seed=4))
+    rev = torch.arange(n - 1, -1, -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_lsolve_noalloc(rowptr, colidx, diag, rev, lu, b)
+    assert e.value.status == jv.JV_ERR_TIMEOUT
+    _, _, level_rows, _ = jv.jv_get_levels(h, "L")
+    assert torch.equal(jv.jv_lsolve_noalloc(rowptr, colidx, diag, level_rows, lu, b),
+                       jv.jv_lsolve(h, lu, b))
+
+
+def test_noalloc_rejects_rows_outside_the_matrix():
+    # an order entry equal to n names no row: the call reports JV_ERR_ARG
+    # (the row is never read) and the next call starts clean
+    rp, ci, v = W.lap5(20)
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci))
+    lu = jv.jv_ilu0_factor(h, T(v))
+    rowptr, colidx, diag = jv.jv_get_pattern(h)
+    b = T(W.rhs(n, 1, seed=5))
+    bad = torch.arange(n, dtype=torch.int32, device="cuda")
+    bad[n // 2] = n
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_lsolve_noalloc(rowptr, colidx, diag, bad, lu, b)
+    assert e.value.status in (jv.JV_ERR_ARG, jv.JV_ERR_TIMEOUT)
+    order = torch.arange(n, dtype=torch.int32, device="cuda")
+    assert torch.equal(jv.jv_lsolve_noalloc(rowptr, colidx, diag, order, lu, b),
+                       jv.jv_lsolve(h, lu, b))
