@@ -152,6 +152,20 @@ typedef struct {
                                        buffers and mode replay it (up to 16 graphs per
                                        handle; inside a stream capture of the caller's own
                                        the launches go into that capture). */
+    int exact_division;             /* 1: the FP64 factor and the FP64 U / U^T solves divide
+                                       by each pivot as Fig. 1 and back substitution do,
+                                       every operation in the serial algorithm's order, so
+                                       FP64 results equal the serial algorithm's bit for
+                                       bit.  0 (default): the FP64 factor's row k computes
+                                       1/u_kk once, by Newton's iteration, when u_kk is
+                                       final and publishes it beside the factor; every
+                                       multiplier is then l_ik = a_ik * (1/u_kk), and the
+                                       U / U^T solves multiply by 1/u_ii, computed before a
+                                       row's operands arrive.  Each such result is within a
+                                       few units in the last place of the quotient; the
+                                       division sequence it replaces is the longest run of
+                                       FP64 work on the critical path.  FP32 always divides
+                                       (its pipe is full width). */
 } jv_options;
 
 typedef struct {

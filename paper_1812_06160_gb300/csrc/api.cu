@@ -57,6 +57,7 @@ void destroy_handle(jv_handle h) {
     if (h->fscratch) cudaFree(h->fscratch);
     if (h->xscratch) cudaFree(h->xscratch);
     if (h->pscratch) cudaFree(h->pscratch);
+    if (h->rinv) cudaFree(h->rinv);
     if (h->ticket) cudaFree(h->ticket);
     if (h->status) cudaFree(h->status);
     if (h->h_status) cudaFreeHost(h->h_status);
@@ -99,6 +100,7 @@ void jv_default_options(jv_options *opt) {
     opt->stage_position = 0.0;
     opt->er_corner = 0;
     opt->no_graphs = 0;
+    opt->exact_division = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {

@@ -27,6 +27,16 @@
 // rows too large for the warp's shared memory work in a global scratch area
 // and await each operand when they use it.
 //
+// Reciprocal pivots (RCP, FP64 unless jv_options.exact_division): a finished
+// row k also computes y_k = 1/u_kk (Newton's iteration, rcp_newton) and
+// publishes it in rinv[k]; a dependant polls y_k instead of u_kk and forms
+// l_rk = a_rk * y_k.  On this part a warp instruction of the FP64 pipe costs
+// 64 cycles whatever its active lanes, and the three correctly rounded
+// divisions of a 7-point row were the longest run of FP64 work on the
+// critical path of every level; one reciprocal per row (five instructions)
+// and one multiply per step replace them.  Each multiplier is then within a
+// few units in the last place of the quotient instead of equal to it.
+//
 // LEVEL mode: one launch per level of lower(A) (Sec. III-A: up-looking ILU has
 // the dependency structure of a triangular solve).  SYNCFREE mode (the
 // point-to-point synchronisation of Sec. III-A, Fig. 4): one persistent
@@ -70,6 +80,8 @@ struct FactorArgs {
     void *pscratch;               // operands of rows too long for shared memory
     long long npairs_total;       // offset of the u_kk area in pscratch
     const unsigned char *row_pull; // per row: take the pull form
+    const int *colidx;            // column of every entry (RCP: the pivot row k of entry (r, k))
+    void *rinv;                   // RCP: 1/u_kk of every row k (sentinel-filled in SYNCFREE mode)
 };
 
 template <class T> struct RN;
@@ -131,7 +143,7 @@ __device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, T d) {
 }
 
 // ------------------------------------------------------- one lane per row
-template <class TV, class TL, bool SF, int W, int S>
+template <class TV, class TL, bool SF, int W, int S, bool RCP>
 __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi, unsigned gate,
                                              unsigned char *smem) {
     using B = Bits<TL>;
@@ -150,6 +162,9 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     int r = 0, rs = 0, len = 0, nl = 0, m = 0, got = 0;
     unsigned tmask = 0;                 // row-local entries some step of the row updates
     TL *lu = static_cast<TL *>(a.lu);
+    TL *rinv = static_cast<TL *>(a.rinv);
+    // operand e of the row: y_k (RCP) or u_kk for a step, u_kq for a pair
+    auto src = [&](int e, int pos_) -> const TL * { return (RCP && e < nl ? rinv : lu) + pos_; };
     if (!done) {
         r = __ldg(a.rows + pos);
         rs = __ldg(a.rowptr + r);
@@ -165,7 +180,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 #pragma unroll
         for (int e = 0; e < S; ++e) {
             if (e < len) v[e] = (TL)__ldg(vals + rs + e);
-            if (e < nl) kd[e] = __ldg(a.kdiag + rs + e);
+            if (e < nl) kd[e] = RCP ? __ldg(a.colidx + rs + e) : __ldg(a.kdiag + rs + e);
             if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
             if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
         }
@@ -192,7 +207,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         if (SF && gate) {               // bring the operands' lines into L2 before sleeping
 #pragma unroll
             for (int e = 0; e < S; ++e) {
-                if (e < nl) prefetch_l2(lu + kd[e]);
+                if (e < nl) prefetch_l2(src(e, kd[e]));
                 if (e < np) prefetch_l2(lu + pr[e].y);
             }
         }
@@ -202,20 +217,26 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     auto finish = [&]() {
         int j = 0;
         for (int p = 0; p < nl; ++p) {
-            const TL lik = RN<TL>::div(V(p), V(len + p));
+            const TL lik = RCP ? V(p) * V(len + p) : RN<TL>::div(V(p), V(len + p));
             for (const int j1 = STEP_END(p); j < j1; ++j) {
                 const int t = TGT(j);
                 V(t) = RN<TL>::fms(lik, V(len + nl + j), V(t));
             }
             V(p) = lik;
         }
-        // the updated U entries, the diagonal first, then the L part
+        // the updated U entries, the diagonal first, then (RCP) the pivot's
+        // reciprocal, then the L part
         if (!SF || r != a.fault_row) {
             for (int e = nl; e < len; ++e)
                 if ((tmask >> e) & 1u) {
                     if (SF) publish<TL>(lu + rs + e, V(e));
                     else lu[rs + e] = V(e);
                 }
+            if constexpr (RCP) {
+                const TL y = rcp_newton(V(nl));
+                if (SF) publish<TL>(rinv + r, y);
+                else rinv[r] = y;
+            }
         }
         pivot_check<TL>(a, r, V(nl));
         for (int e = 0; e < nl; ++e) lu[rs + e] = V(e);
@@ -236,7 +257,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 #pragma unroll
             for (int k = 0; k < W; ++k)
                 if (!done && k < m && !((seen >> k) & 1u))
-                    u[k] = ld_relaxed(reinterpret_cast<const U *>(lu + op[k]));
+                    u[k] = ld_relaxed(reinterpret_cast<const U *>(src(k, op[k])));
 #pragma unroll
             for (int k = 0; k < W; ++k)
                 if (!done && k < m && !((seen >> k) & 1u) && u[k] != B::kSent) {
@@ -282,7 +303,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             // published together, so they are all polled in the same round
 #pragma unroll
             for (int k = 0; k < W; ++k)
-                if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(lu + OPOS(wb + k));
+                if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(src(wb + k, OPOS(wb + k)));
             bool ok = true;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
@@ -321,7 +342,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 }
 
 // ------------------------------------------------------- one warp per row
-template <class TV, class TL, bool SF, int S>
+template <class TV, class TL, bool SF, int S, bool RCP>
 __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsigned gate,
                                             unsigned char *smem) {
     using B = Bits<TL>;
@@ -335,6 +356,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     const int m = nl + np;
     bool fail = false;                 // a wait gave up: publish nothing
     TL *lu = static_cast<TL *>(a.lu);
+    TL *rinv = static_cast<TL *>(a.rinv);
     const TV *vals = static_cast<const TV *>(a.vals);
     const size_t need = (size_t)(len + m) * sizeof(TL) + (size_t)(np + nl) * sizeof(int);
     const bool fast = need <= (size_t)warp_smem<S>();
@@ -355,15 +377,17 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
                 const int e = e0 + k * kWarp + lane;
                 src[k] = -1;
                 if (e < m) {
-                    src[k] = e < nl ? __ldg(a.kdiag + rs + e) : __ldg(a.pairs + j0 + e - nl).y;
-                    u[k] = first_read<TL, SF>(lu + src[k]);
+                    src[k] = e < nl ? (RCP ? __ldg(a.colidx + rs + e) : __ldg(a.kdiag + rs + e))
+                                    : __ldg(a.pairs + j0 + e - nl).y;
+                    u[k] = first_read<TL, SF>((RCP && e < nl ? rinv : lu) + src[k]);
                 }
             }
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k)
                 if (src[k] >= 0) {
-                    if (SF) u[k] = settle<TL>(lu + src[k], u[k], a, r, fail);
-                    uv[e0 + k * kWarp + lane] = B::from(u[k]);
+                    const int e = e0 + k * kWarp + lane;
+                    if (SF) u[k] = settle<TL>((RCP && e < nl ? rinv : lu) + src[k], u[k], a, r, fail);
+                    uv[e] = B::from(u[k]);
                 }
         }
     }
@@ -374,10 +398,10 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         if (fast) {
             ukk = uv[p];
         } else {
-            const TL *src = lu + __ldg(a.kdiag + rs + p);
+            const TL *src = RCP ? rinv + __ldg(a.colidx + rs + p) : lu + __ldg(a.kdiag + rs + p);
             ukk = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
         }
-        const TL lik = RN<TL>::div(w[p], ukk);
+        const TL lik = RCP ? w[p] * ukk : RN<TL>::div(w[p], ukk);
         const int je = fast ? send[p] : __ldg(a.pair_ptr + rs + p + 1) - j0;
         // the targets of one step are distinct -- except, with MILU, the
         // diagonal, which lane 0 then updates alone, in the listed order
@@ -419,6 +443,11 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     __syncwarp();
     if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) pivot_check<TL>(a, r, w[nl]);
+    if (RCP && lane == 0 && (!SF || r != a.fault_row)) {
+        const TL y = rcp_newton(w[nl]);
+        if (SF) publish<TL>(rinv + r, y);
+        else rinv[r] = y;
+    }
     for (int e = lane; e < len; e += kWarp) {
         const TL v = w[e];
         if (!SF || e < nl) lu[rs + e] = v;
@@ -438,7 +467,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
 // entry pulls its updates at once.  The row's operands (every u_q, every
 // u_kk) are read first, in parallel, each through its bounded wait, into
 // shared memory (or the operand scratch for a row too long for it).
-template <class TV, class TL, bool SF, int S>
+template <class TV, class TL, bool SF, int S, bool RCP>
 __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, unsigned gate,
                                                  unsigned char *smem) {
     using B = Bits<TL>;
@@ -464,8 +493,9 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     }
     for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
-    for (int e = lane; e < nl; e += kWarp) {
-        const TL *src = lu + __ldg(a.kdiag + rs + e);
+    TL *rinv = static_cast<TL *>(a.rinv);
+    for (int e = lane; e < nl; e += kWarp) {               // u_kk, or its reciprocal (RCP)
+        const TL *src = RCP ? rinv + __ldg(a.colidx + rs + e) : lu + __ldg(a.kdiag + rs + e);
         ukk[e] = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
     }
     for (int e = lane; e < nq; e += kWarp) {
@@ -493,7 +523,7 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
                 TL acc = w[e];
                 for (int k = t0; k < t1; ++k)
                     acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
-                w[e] = RN<TL>::div(acc, ukk[e]);
+                w[e] = RCP ? acc * ukk[e] : RN<TL>::div(acc, ukk[e]);
                 done = true;
             }
             __syncwarp();
@@ -510,6 +540,11 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     __syncwarp();
     if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) pivot_check<TL>(a, r, w[nl]);
+    if (RCP && lane == 0 && (!SF || r != a.fault_row)) {
+        const TL y = rcp_newton(w[nl]);
+        if (SF) publish<TL>(rinv + r, y);
+        else rinv[r] = y;
+    }
     for (int e = lane; e < len; e += kWarp) {
         const TL v = w[e];
         if (!SF || e < nl) lu[rs + e] = v;
@@ -518,32 +553,32 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     __syncwarp();                                              // shared memory reusable
 }
 
-template <class TV, class TL, bool SF, int W, int S>
+template <class TV, class TL, bool SF, int W, int S, bool RCP>
 __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsigned char *smem) {
     const int lo = __ldg(a.task_lo + task), hi = __ldg(a.task_hi + task);
     const unsigned gate = SF ? sf_gate_of(a.task_lev, a.task_ptr, a.gate_levels, a.task_begin, task) : 0u;
     if (hi & kLongBit) {
         if (a.tpairs && __ldg(a.row_pull + __ldg(a.rows + lo)))
-            factor_warp_pull<TV, TL, SF, S>(a, lo, gate, smem);
+            factor_warp_pull<TV, TL, SF, S, RCP>(a, lo, gate, smem);
         else
-            factor_warp<TV, TL, SF, S>(a, lo, gate, smem);
+            factor_warp<TV, TL, SF, S, RCP>(a, lo, gate, smem);
     }
-    else factor_lanes<TV, TL, SF, W, S>(a, lo, hi, gate, smem);
+    else factor_lanes<TV, TL, SF, W, S, RCP>(a, lo, hi, gate, smem);
     __syncwarp();
 }
 
-template <class TV, class TL, bool SF, int W, int S>
+template <class TV, class TL, bool SF, int W, int S, bool RCP>
 __global__ void __launch_bounds__(kBlock, 1) k_ilu0(FactorArgs a) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int wib = threadIdx.x >> 5;
     unsigned char *smem = dyn_smem + (size_t)wib * warp_smem<S>();
     if (SF) {
         sf_for_each_task(a.ticket, a.task_begin, a.task_end,
-                         [&](int task) { factor_task<TV, TL, SF, W, S>(a, task, smem); });
+                         [&](int task) { factor_task<TV, TL, SF, W, S, RCP>(a, task, smem); });
         sf_finish(a.ticket);
     } else {
         const int task = a.task_begin + blockIdx.x * kWarpsPerBlock + wib;
-        if (task < a.task_end) factor_task<TV, TL, SF, W, S>(a, task, smem);
+        if (task < a.task_end) factor_task<TV, TL, SF, W, S, RCP>(a, task, smem);
     }
 }
 
@@ -569,22 +604,30 @@ int ensure_scratch(jv_handle h) {
     return JV_OK;
 }
 
-template <class TV, class TL, bool SF, int W, int S>
+template <class TV, class TL, bool SF, int W, int S, bool RCP>
 int launch_w(int grid, cudaStream_t s, const FactorArgs &a) {
-    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 block_smem<S>()));
+    JV_CUDA(cudaFuncSetAttribute(k_ilu0<TV, TL, SF, W, S, RCP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, block_smem<S>()));
     count_launch();
-    k_ilu0<TV, TL, SF, W, S><<<grid, kBlock, block_smem<S>(), s>>>(a);
+    k_ilu0<TV, TL, SF, W, S, RCP><<<grid, kBlock, block_smem<S>(), s>>>(a);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }
+template <class TV, class TL, bool SF, bool RCP>
+int launch_r(int window, int slot, int grid, cudaStream_t s, const FactorArgs &a) {
+    if (slot > kLaneSlot)
+        return window <= 4 ? launch_w<TV, TL, SF, 4, kLaneSlotWide, RCP>(grid, s, a)
+                           : launch_w<TV, TL, SF, kPoll, kLaneSlotWide, RCP>(grid, s, a);
+    return window <= 4 ? launch_w<TV, TL, SF, 4, kLaneSlot, RCP>(grid, s, a)
+                       : launch_w<TV, TL, SF, kPoll, kLaneSlot, RCP>(grid, s, a);
+}
+// reciprocal pivots for an FP64 factor unless exact division is asked for
 template <class TV, class TL, bool SF>
 int launch(int window, int slot, int grid, cudaStream_t s, const FactorArgs &a) {
-    if (slot > kLaneSlot)
-        return window <= 4 ? launch_w<TV, TL, SF, 4, kLaneSlotWide>(grid, s, a)
-                           : launch_w<TV, TL, SF, kPoll, kLaneSlotWide>(grid, s, a);
-    return window <= 4 ? launch_w<TV, TL, SF, 4, kLaneSlot>(grid, s, a)
-                       : launch_w<TV, TL, SF, kPoll, kLaneSlot>(grid, s, a);
+    if constexpr (sizeof(TL) == 8) {
+        if (a.rinv) return launch_r<TV, TL, SF, true>(window, slot, grid, s, a);
+    }
+    return launch_r<TV, TL, SF, false>(window, slot, grid, s, a);
 }
 
 template <class TV, class TL>
@@ -613,6 +656,22 @@ int run(jv_handle h, const void *vals, void *lu) {
             }
             h->pscratch_bytes = need;
         }
+    }
+    // reciprocal pivots: FP64 factors unless exact division is asked for
+    const bool rcp = sizeof(TL) == 8 && !h->opt.exact_division;
+    if (rcp && h->rinv_bytes < (size_t)h->n * sizeof(TL)) {
+        if (h->rinv) {
+            JV_CUDA(cudaStreamSynchronize(s));
+            cudaFree(h->rinv);
+            h->rinv = nullptr;
+            h->rinv_bytes = 0;
+        }
+        if (cudaMalloc(&h->rinv, (size_t)h->n * sizeof(TL) + 16) != cudaSuccess) {
+            cudaGetLastError();
+            h->rinv = nullptr;
+            return JV_ERR_NOMEM;
+        }
+        h->rinv_bytes = (size_t)h->n * sizeof(TL);
     }
     const void *const user_vals = vals;
     void *const copy = inplace ? static_cast<char *>(h->fscratch) + (size_t)h->nnz * sizeof(double)
@@ -655,6 +714,8 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.pscratch = h->pscratch;
     a.npairs_total = h->npairs;
     a.row_pull = h->row_pull;
+    a.colidx = h->colidx;
+    a.rinv = rcp ? h->rinv : nullptr;
     a.backoff_ns = sf_backoff(h);
     // the upper stage: levels [0, lend), above the Even-Rows corner if any
     const jv_dtype lu_t = sizeof(TL) == 8 ? JV_F64 : JV_F32;
@@ -678,7 +739,9 @@ int run(jv_handle h, const void *vals, void *lu) {
         };
         int rc = JV_OK;
         if (has_sync_free(h, L, lend)) {
-            rc = fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
+            rc = rcp ? fill2_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, h->rinv,
+                                 (size_t)h->n * sizeof(TL) / 4, ~0u, s)
+                     : fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
             if (rc) return rc;
         }
         if (h->opt.mode == JV_MODE_SYNCFREE) {
@@ -701,7 +764,7 @@ int run(jv_handle h, const void *vals, void *lu) {
     const std::vector<unsigned long long> key = {
         1, sizeof(TV), sizeof(TL), (unsigned long long)h->opt.mode, (unsigned long long)(uintptr_t)user_vals,
         (unsigned long long)(uintptr_t)lu, (unsigned long long)(uintptr_t)h->fscratch,
-        (unsigned long long)(uintptr_t)h->pscratch};
+        (unsigned long long)(uintptr_t)h->pscratch, (unsigned long long)(uintptr_t)a.rinv};
     return graph_run(h, key, seq);
 }
 

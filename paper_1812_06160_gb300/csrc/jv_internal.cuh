@@ -247,6 +247,28 @@ template <> struct Bits<float> {
     }
 };
 
+// 1/d for the FP64 factor and back substitution (jv_options.exact_division =
+// 0): Newton's iteration for the reciprocal, y <- y + y (1 - d y), which
+// squares the relative error at every step, started from the approximate
+// reciprocal the hardware provides (PTX rcp.approx.ftz.f64).  Two steps take
+// any seed better than 2^-14 to the rounding level: the result is within one
+// unit in the last place of 1/d.  Zero, subnormal, huge and non-finite inputs
+// (exponent outside +-1000, where the seed may flush to zero or 1/d be
+// subnormal) take the correctly rounded __drcp_rn instead.  Five FP64-pipe
+// instructions in the common case, against about three times as many for a
+// correctly rounded division.
+__device__ __forceinline__ double rcp_newton(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned ex = (unsigned)(u >> 52) & 0x7ffu;
+    if (ex < 1023u - 1000u || ex > 1023u + 1000u) return __drcp_rn(d);
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    double e = __fma_rn(-d, y, 1.0);
+    y = __fma_rn(y, e, y);
+    e = __fma_rn(-d, y, 1.0);
+    return __fma_rn(y, e, y);
+}
+
 // f(i) = a[i + ai] + ad: one kernel can walk a CSR or CSC sub-range of row or
 // column i (e.g. the strictly lower part of row i is [rowptr[i], diag[i])).
 struct Span {
@@ -417,6 +439,8 @@ struct jv_handle_s {
     void *xscratch = nullptr;                // FP32 solution of FP32-factor solves into FP64 x
     size_t xscratch_bytes = 0;
     void *pscratch = nullptr;                // operands of long rows: [npairs + nnz] elements
+    void *rinv = nullptr;                    // FP64 factor: 1/u_kk of every row, published by
+    size_t rinv_bytes = 0;                   // the row (sentinel-filled in sync-free mode)
     int fslot = jv::kLaneSlot;               // factor one-lane slot (kLaneSlot or kLaneSlotWide)
     size_t pscratch_bytes = 0;
     // scratch shared by the sync-free kernels
@@ -425,7 +449,7 @@ struct jv_handle_s {
     unsigned long long *status = nullptr;    // device status word
     unsigned long long *h_status = nullptr;  // pinned host mirror
     int bad_row = -1;                        // row of the last analysis error
-    int num_sms = 152;
+    int num_sms = 0;                         // queried in jv_analyze
     jv::Workspace *ws = nullptr;
     std::vector<jv::GraphEntry> graphs;      // replayable per-level launch sequences
     unsigned long long graph_clock = 0;
@@ -457,6 +481,8 @@ template <class T> int halloc_n(jv_handle h, T **p, size_t count) {
 // multiprocessors of the current device (queried once per device)
 int current_device_sms();
 int fill_u32(void *p, size_t count_u32, unsigned v, cudaStream_t s);
+// two ranges in one launch
+int fill2_u32(void *p0, size_t count0_u32, void *p1, size_t count1_u32, unsigned v, cudaStream_t s);
 int iota_i32(int *p, int n, cudaStream_t s);
 // exclusive scan of in[0..m) into out[0..m]; out[m] = total.  tmp: >= scan_tmp_ints(m)
 size_t scan_tmp_ints(int m);

@@ -12,9 +12,7 @@ namespace jv {
 std::atomic<unsigned long long> g_launches{0};
 
 // ------------------------------------------------------------------- fill
-__global__ void k_fill_u32(unsigned *p, size_t n, unsigned v) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    size_t stride = (size_t)gridDim.x * blockDim.x;
+__device__ __forceinline__ void fill_range(unsigned *p, size_t n, unsigned v, size_t i, size_t stride) {
     uintptr_t addr = (uintptr_t)p;
     size_t head = ((16 - (addr & 15)) & 15) / 4;
     if (head > n) head = n;
@@ -24,6 +22,16 @@ __global__ void k_fill_u32(unsigned *p, size_t n, unsigned v) {
     uint4 vv = make_uint4(v, v, v, v);
     for (size_t j = i; j < nv; j += stride) q[j] = vv;
     for (size_t j = head + nv * 4 + i; j < n; j += stride) p[j] = v;
+}
+
+__global__ void k_fill_u32(unsigned *p, size_t n, unsigned v) {
+    fill_range(p, n, v, blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+// two ranges in one launch: grid row y fills range y
+__global__ void k_fill2_u32(unsigned *p0, size_t n0, unsigned *p1, size_t n1, unsigned v) {
+    fill_range(blockIdx.y ? p1 : p0, blockIdx.y ? n1 : n0, v,
+               blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 int current_device_sms() {
@@ -52,6 +60,18 @@ int fill_u32(void *p, size_t count, unsigned v, cudaStream_t s) {
     if (grid > cap) grid = cap;
     count_launch();
     k_fill_u32<<<grid, kBlock, 0, s>>>((unsigned *)p, count, v);
+    JV_CHECK_LAUNCH();
+    return JV_OK;
+}
+
+int fill2_u32(void *p0, size_t count0, void *p1, size_t count1, unsigned v, cudaStream_t s) {
+    const size_t big = count0 > count1 ? count0 : count1;
+    if (big == 0) return JV_OK;
+    int grid = grid_for((long long)(big / 4 + 1), kBlock);
+    const int cap = current_device_sms() * 8;    // 2 x 8 CTAs per SM, grid-stride beyond
+    if (grid > cap) grid = cap;
+    count_launch();
+    k_fill2_u32<<<dim3(grid, 2), kBlock, 0, s>>>((unsigned *)p0, count0, (unsigned *)p1, count1, v);
     JV_CHECK_LAUNCH();
     return JV_OK;
 }

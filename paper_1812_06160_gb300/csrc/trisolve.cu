@@ -9,7 +9,8 @@
 // csc2csr).  The order is the one the serial substitution uses (ascending
 // columns; descending rows for L^T) and every update is one fused
 // multiply-add, so the result equals the serial solve bit for bit; only the
-// loads run in parallel.
+// loads run in parallel.  (FP64 U and U^T solves multiply by 1/u_rr unless
+// jv_options.exact_division asks for the division: see TriArgs::rcp.)
 //
 // Work list (see Bins): a short task holds up to 32 rows of one level, one
 // lane per row.  Every lane polls the next W dependencies of its own row (a
@@ -41,6 +42,8 @@ struct TriArgs {
     const int *vmap;       // CSC -> CSR value position, or nullptr
     const int *diag;
     int unit;              // 1: unit diagonal (L, L^T)
+    int rcp;               // FP64 U, U^T: multiply by 1/u_rr (rcp_newton, computed before the
+                           // row's operands arrive) instead of dividing by u_rr
     int reverse;           // 1: walk the range from its end (L^T)
     const int *rows, *task_lo, *task_hi;
     int task_begin, task_end;
@@ -113,6 +116,25 @@ __device__ __forceinline__ TL load_val(const TriArgs &a, int q) {
     return a.vmap ? __ldg(lu + __ldg(a.vmap + q)) : __ldg(lu + q);
 }
 
+// The diagonal a row finishes with: u_rr, or 1/u_rr when the solve multiplies.
+template <class TL>
+__device__ __forceinline__ TL load_diag(const TriArgs &a, int r) {
+    const TL d = __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    if constexpr (sizeof(TL) == 8) {
+        if (a.rcp) return rcp_newton(d);
+    }
+    return d;
+}
+// x_r from the finished sum s and load_diag's d
+template <class TL>
+__device__ __forceinline__ TL finish_row(const TriArgs &a, TL s, TL d) {
+    if (a.unit) return s;
+    if constexpr (sizeof(TL) == 8) {
+        if (a.rcp) return s * d;
+    }
+    return RN<TL>::div(s, d);
+}
+
 template <class TL, class TX>
 __device__ __forceinline__ void store_x(const TriArgs &a, bool sf, TX *p, int r, TL v) {
     if (sf) {
@@ -142,7 +164,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         qb = a.beg.at(r);
         len = a.end.at(r) - qb;
         s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
-        if (!a.unit) d = __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+        if (!a.unit) d = load_diag<TL>(a, r);
         if (len > 0) {               // first window: indices and values
             wend = min(W, len);
 #pragma unroll
@@ -201,7 +223,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
 #pragma unroll
                 for (int k = 0; k < W; ++k)
                     if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
-                store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
             }
             return;
         }
@@ -230,7 +252,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                     for (int k = 0; k < W; ++k)
                         if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
                 }
-                store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
                 done = true;
             } else if (!done) {
                 if (rounds++ == 0) t0 = clock64();
@@ -287,7 +309,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                 }
             }
             if (e == len) {
-                store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
                 done = true;
             }
         }
@@ -318,7 +340,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     const int qb = a.beg.at(r);
     const int len = a.end.at(r) - qb;
     TL s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
-    const TL d = a.unit ? (TL)1 : __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r);
     bool fail = false;                 // a wait gave up: publish nothing
     for (int c0 = 0; c0 < len; c0 += CH) {
         int q[kUnroll];
@@ -355,7 +377,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
             }
     }
     if (SF && __any_sync(0xffffffffu, fail)) return;
-    if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, a.unit ? s : RN<TL>::div(s, d));
+    if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
 }
 
 template <class TL, class TB, class TX, bool SF, int W, bool ONE>
@@ -389,7 +411,7 @@ __device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
     const size_t ld = (size_t)a.nrhs;
     TX *x = static_cast<TX *>(a.x);
     const TB *b = static_cast<const TB *>(a.b);
-    const TL d = a.unit ? (TL)1 : __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r);
     for (int c0 = 0; c0 < a.nrhs; c0 += 32) {
         const int c = c0 + lane;
         const bool ok = c < a.nrhs;
@@ -420,7 +442,7 @@ __device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
                 }
             }
         }
-        if (ok && !fail) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, a.unit ? s : RN<TL>::div(s, d));
+        if (ok && !fail) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, finish_row<TL>(a, s, d));
     }
 }
 
@@ -487,6 +509,7 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
     a.backoff_ns = sf_backoff(h);
+    a.rcp = sizeof(TL) == 8 && !h->opt.exact_division;
     // a one-column solve may end in an Even-Rows corner: the upper stage
     // then runs the levels above it
     const SolveCorner *C = multi ? nullptr : solve_corner_of(h, structure, sizeof(TL), sizeof(TX));

@@ -10,8 +10,13 @@ SCHEDULES = ("level", "syncfree", "band")
 def analyze(jv, rowptr, colidx, schedule, **kw):
     """Handle for one schedule: 'level' (one launch per level), 'syncfree'
     (one persistent launch over level-ordered tasks), 'band' (sync-free band
-    schedule, forced with a small band so it meets every pattern)."""
+    schedule, forced with a small band so it meets every pattern).  The
+    handle divides by every pivot as the serial algorithm does
+    (exact_division) unless the caller asks otherwise: the bit-exact tests
+    compare that mode with the oracle, the tests of the default mode pass
+    exact_division=False and compare within tolerance."""
     import torch
+    kw.setdefault("exact_division", True)
     rp = torch.tensor(np.asarray(rowptr), device="cuda")
     ci = torch.tensor(np.asarray(colidx), device="cuda")
     if schedule == "level":

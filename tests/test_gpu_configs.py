@@ -9,7 +9,7 @@ import torch
 
 import oracle as O
 import workloads as W
-from jvutil import analyze, max_rel
+from jvutil import analyze, close, max_rel
 
 jv = pytest.importorskip("paper_1812_06160_gb300")
 pytestmark = pytest.mark.gpu
@@ -36,11 +36,15 @@ def _levels_match(h, rp, ci):
         assert np.array_equal(grows.cpu().numpy(), rows)
 
 
-def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False):
+def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False, exact=False):
+    """FP64 with exact division, and FP32 (which always divides): factor and
+    solves bit-exact with the oracle.  FP64 in the default mode (reciprocal
+    pivots): every entry within 1e-12 relative of the oracle's (row-scaled
+    floor of jvutil.close), the raw largest error printed."""
     if mode == "auto":        # the benchmark's configuration: sync-free, schedule chosen by the analysis
-        h = jv.jv_analyze(T(rp), T(ci), reorder=reorder)
+        h = jv.jv_analyze(T(rp), T(ci), reorder=reorder, exact_division=exact)
     else:
-        h = analyze(jv, rp, ci, mode, reorder=reorder)
+        h = analyze(jv, rp, ci, mode, reorder=reorder, exact_division=exact)
     if reorder:
         _, _, _, perm = O.level_sets(rp, ci)
         _, rp, ci, vmap = O.permute(rp, ci, perm)
@@ -55,7 +59,13 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False):
         olu, st, _ = O.ilu0(rp, ci, v.astype(np.float32), diag, dtype=np.float32)
         lu = jv.jv_ilu0_factor(h, T(v), lu_dtype=torch.float32)
     assert st == 0
-    assert np.array_equal(lu.cpu().numpy(), olu)
+    bit_exact = exact or dtype != np.float64
+    if bit_exact:
+        assert np.array_equal(lu.cpu().numpy(), olu)
+    else:
+        ok, err = close(lu.cpu().numpy(), olu)
+        print(f"factor: largest relative error {err:.2e} (raw {max_rel(lu.cpu().numpy(), olu):.2e})")
+        assert ok, err
     olu64 = olu.astype(np.float64)
     bb = b.astype(dtype)
     y = jv.jv_lsolve(h, lu, T(bb))
@@ -63,8 +73,14 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False):
     oy = O.lsolve(rp, ci, diag, olu64, bb.astype(np.float64))
     oz = O.usolve(rp, ci, diag, olu64, oy)
     if dtype == np.float64:
-        assert np.array_equal(y.cpu().numpy(), oy)
-        assert np.array_equal(z.cpu().numpy(), oz)
+        if bit_exact:
+            assert np.array_equal(y.cpu().numpy(), oy)
+            assert np.array_equal(z.cpu().numpy(), oz)
+        else:
+            for name, got, want in (("lsolve", y, oy), ("usolve", z, oz)):
+                ok, err = close(got.cpu().numpy(), want)
+                print(f"{name}: largest relative error {err:.2e}")
+                assert ok, (name, err)
         x = W.rhs(len(rp) - 1, 1, seed=21)
         s = jv.jv_spmv(h, T(v), T(x)).cpu().numpy()
         assert np.array_equal(s, O.spmv(rp, ci, v, x))
@@ -80,15 +96,21 @@ def test_c2_lap7_128_fp64(mode):
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], mode)
 
 
+def test_c2_lap7_128_fp64_exact_division():
+    c = cfg("c2")
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", exact=True)
+
+
 def test_c2_lap7_128_fp64_reordered():
     c = cfg("c2")
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", reorder=True)
 
 
+@pytest.mark.parametrize("exact", [False, True])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-def test_c3_cd27_96(dtype):
+def test_c3_cd27_96(dtype, exact):
     c = cfg("c3")
-    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", dtype=dtype)
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", dtype=dtype, exact=exact)
 
 
 def test_c5_aniso_1024_32rhs():
@@ -100,7 +122,7 @@ def test_c5_aniso_1024_32rhs():
     rp, ci, v, B, g = c["rowptr"], c["colidx"], c["vals"], c["b"], c["g"]
     diag = O.diag_ptr(rp, ci)
     olu32, _, _ = O.ilu0(rp, ci, v.astype(np.float32), diag, dtype=np.float32)
-    h = jv.jv_analyze(T(rp), T(ci))
+    h = jv.jv_analyze(T(rp), T(ci), exact_division=True)
     lu = jv.jv_ilu0_factor(h, T(v), lu_dtype=torch.float32)
     assert np.array_equal(lu.cpu().numpy(), olu32)
     lu64 = olu32.astype(np.float64)
@@ -162,4 +184,5 @@ def test_c3_fgmres30_full_size():
 def test_c4_powerlaw_1e6():
     c = cfg("c4")
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto")
+    _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", exact=True)
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", dtype=np.float32)

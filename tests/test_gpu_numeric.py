@@ -38,6 +38,44 @@ def test_factor_fp64_bit_exact(case, mode):
 
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_factor_fp64_reciprocal_pivots_within_1e12(case, mode):
+    # the default FP64 factor multiplies by each pivot's reciprocal: every
+    # entry within 1e-12 relative of the oracle's divisions
+    _, rp, ci, v = case
+    h = analyze(jv, rp, ci, mode, exact_division=False)
+    lu = jv.jv_ilu0_factor(h, T(v)).cpu().numpy()
+    olu, st, _ = O.ilu0(rp, ci, v)
+    assert st == 0
+    ok, err = close(lu, olu)
+    assert ok, err
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("nrhs", [1, 3, 33])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_solves_fp64_reciprocal_diagonal(case, nrhs, mode):
+    # default mode: the L and L^T solves (no division) stay bit-exact; the U
+    # and U^T solves multiply by 1/u_ii and stay within 1e-12 relative
+    _, rp, ci, v = case
+    n = len(rp) - 1
+    h = analyze(jv, rp, ci, mode, exact_division=False)
+    olu, _, _ = O.ilu0(rp, ci, v)
+    diag = O.diag_ptr(rp, ci)
+    b = W.rhs(n, nrhs, seed=17 + nrhs)
+    lu, bt = T(olu), T(b)
+    for name, ofn, exact in (("jv_lsolve", O.lsolve, True), ("jv_usolve", O.usolve, False),
+                             ("jv_lsolve_t", O.lsolve_t, True), ("jv_usolve_t", O.usolve_t, False)):
+        x = getattr(jv, name)(h, lu, bt).cpu().numpy()
+        want = ofn(rp, ci, diag, olu, b)
+        if exact:
+            assert np.array_equal(x, want), (name, close(x, want)[1])
+        else:
+            ok, err = close(x, want)
+            assert ok, (name, err)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_factor_fp32_bit_exact_to_fp32_twin(case, mode):
     _, rp, ci, v = case
     h = analyze(jv, rp, ci, mode)
@@ -99,7 +137,7 @@ def test_solves_fp32_and_mixed(case, mode):
 def test_spmv(case):
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci))
+    h = jv.jv_analyze(T(rp), T(ci), exact_division=True)
     x = W.rhs(n, 1, seed=3)
     y0 = W.rhs(n, 1, seed=4)
     scale = O.spmv(rp, ci, np.abs(v), np.abs(x)) + np.abs(y0)
@@ -122,7 +160,7 @@ def test_masked_outer(case, nrhs):
     # ones (powerlaw6000) the warp-per-row kernel
     _, rp, ci, _ = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci))
+    h = jv.jv_analyze(T(rp), T(ci), exact_division=True)
     diag = O.diag_ptr(rp, ci)
     a, b = W.rhs(n, nrhs, seed=1), W.rhs(n, nrhs, seed=2)
     for which in (0, 1):
@@ -151,7 +189,7 @@ def test_reordered_factor_and_solve(case):
     up to summation order)."""
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), reorder=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True)
     _, _, _, perm = O.level_sets(rp, ci)
     iperm, brp, bci, vmap = O.permute(rp, ci, perm)
     vb = jv.jv_permute_values(h, T(v))
