@@ -117,6 +117,13 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # nvidia-smi takes a while to start: let its first sample land before
+        # the timed region begins, so the samples cover that region
+        t_end = time.time() + 5.0
+        while self.proc and self.proc.poll() is None and time.time() < t_end:
+            if os.path.exists(self.path) and os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *a):

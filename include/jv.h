@@ -159,13 +159,15 @@ typedef struct {
                                        bit.  0 (default): the FP64 factor's row k computes
                                        1/u_kk once, by Newton's iteration, when u_kk is
                                        final and publishes it beside the factor; every
-                                       multiplier is then l_ik = a_ik * (1/u_kk), and the
-                                       U / U^T solves multiply by 1/u_ii, computed before a
-                                       row's operands arrive.  Each such result is within a
-                                       few units in the last place of the quotient; the
+                                       multiplier is then l_ik = a_ik * (1/u_kk), within a
+                                       few units in the last place of the quotient (the
                                        division sequence it replaces is the longest run of
-                                       FP64 work on the critical path.  FP32 always divides
-                                       (its pipe is full width). */
+                                       FP64 work on the critical path).  The U / U^T solves
+                                       form s / u_ii from 1/u_ii, computed before a row's
+                                       operands arrive, with one correction step
+                                       (Markstein's), which gives the division's result
+                                       with fewer instructions after the last operand.
+                                       FP32 always divides (its pipe is full width). */
 } jv_options;
 
 typedef struct {

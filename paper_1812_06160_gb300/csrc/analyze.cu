@@ -191,6 +191,22 @@ __global__ void k_row_pull(int n, const int *rowptr, const int *diag, const int 
     pull[r] = (unsigned char)(2 * most <= rd - rs ? 1 : 0);
 }
 
+// upd[t] = 1 for every entry some step of Fig. 1 updates (the target of a
+// pair); the others keep A's value from start to end, so a row that reads one
+// as an operand reads it from A's values and never waits for it.  cnt: pairs
+// whose operand q is itself updated (operands that must be awaited).
+__global__ void k_mark_targets(long long np, const int2 *pairs, unsigned char *upd) {
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j < np) upd[pairs[j].x] = 1;
+}
+__global__ void k_count_dynamic(long long np, const int2 *pairs, const unsigned char *upd,
+                                unsigned long long *cnt) {
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool d = j < np && upd[pairs[j].y];
+    const unsigned m = __ballot_sync(0xffffffffu, d);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(cnt, (unsigned long long)__popc(m));
+}
+
 __global__ void k_kdiag(int nnz, const int *colidx, const int *diag, int *kdiag) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < nnz) kdiag[p] = diag[colidx[p]];
@@ -375,7 +391,10 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
     std::vector<int> tlev((size_t)B.ntasks);
     for (int l = 0; l < L.nlev; ++l)
         for (int t = B.h_task_ptr[l]; t < B.h_task_ptr[l + 1]; ++t) tlev[t] = l;
+    std::vector<int> ipos((size_t)n);
+    for (int p = 0; p < n; ++p) ipos[brows[p]] = p;
     JV_TRY(halloc_n(h, &B.rows, n));
+    JV_TRY(halloc_n(h, &B.ipos, n));
     JV_TRY(halloc_n(h, &B.task_lo, B.ntasks));
     JV_TRY(halloc_n(h, &B.task_hi, B.ntasks));
     JV_TRY(halloc_n(h, &B.task_lev, B.ntasks));
@@ -384,6 +403,7 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
     JV_CUDA(cudaMemcpyAsync(B.task_ptr, B.h_task_ptr.data(), (size_t)(L.nlev + 1) * 4,
                             cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaMemcpyAsync(B.rows, brows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    JV_CUDA(cudaMemcpyAsync(B.ipos, ipos.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaMemcpyAsync(B.task_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaMemcpyAsync(B.task_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, s));
     JV_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
@@ -506,6 +526,27 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     count_launch();
     k_kdiag<<<grid_for(nnz, kBlock), kBlock, 0, s>>>(nnz, h->colidx, h->diag, h->kdiag);
     JV_CHECK_LAUNCH();
+    // entries the factor updates, and the pairs whose operand it must await
+    JV_TRY(halloc_n(h, &h->upd, nnz));
+    JV_CUDA(cudaMemsetAsync(h->upd, 0, (size_t)nnz, s));
+    {
+        Temp ctmp;
+        unsigned long long *dc;
+        JV_TRY(ctmp.get(&dc, 1));
+        JV_CUDA(cudaMemsetAsync(dc, 0, 8, s));
+        if (np > 0) {
+            count_launch();
+            k_mark_targets<<<grid_for(np, kBlock), kBlock, 0, s>>>(np, h->pairs, h->upd);
+            JV_CHECK_LAUNCH();
+            count_launch();
+            k_count_dynamic<<<grid_for(np, kBlock), kBlock, 0, s>>>(np, h->pairs, h->upd, dc);
+            JV_CHECK_LAUNCH();
+        }
+        unsigned long long hc = 0;
+        JV_CUDA(cudaMemcpyAsync(&hc, dc, 8, cudaMemcpyDeviceToHost, s));
+        JV_CUDA(cudaStreamSynchronize(s));
+        h->ndyn_pairs = (long long)hc;
+    }
 
     // the same pairs grouped by target: every entry's updates in ascending
     // step (a stable sort of the step-ordered list by target), for the

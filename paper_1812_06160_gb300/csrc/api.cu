@@ -57,7 +57,7 @@ void destroy_handle(jv_handle h) {
     if (h->fscratch) cudaFree(h->fscratch);
     if (h->xscratch) cudaFree(h->xscratch);
     if (h->pscratch) cudaFree(h->pscratch);
-    if (h->rinv) cudaFree(h->rinv);
+    if (h->piv) cudaFree(h->piv);
     if (h->ticket) cudaFree(h->ticket);
     if (h->status) cudaFree(h->status);
     if (h->h_status) cudaFreeHost(h->h_status);

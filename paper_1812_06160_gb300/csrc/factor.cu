@@ -27,10 +27,19 @@
 // rows too large for the warp's shared memory work in a global scratch area
 // and await each operand when they use it.
 //
-// Reciprocal pivots (RCP, FP64 unless jv_options.exact_division): a finished
-// row k also computes y_k = 1/u_kk (Newton's iteration, rcp_newton) and
-// publishes it in rinv[k]; a dependant polls y_k instead of u_kk and forms
-// l_rk = a_rk * y_k.  On this part a warp instruction of the FP64 pipe costs
+// Pivots: a finished row k publishes its pivot in a separate array, at the
+// row's position in the work list (tasks hold consecutive positions, and the
+// rows of consecutive tasks of one level depend on consecutive positions of
+// earlier levels, so a warp's polls of its 32 rows' pivots touch a few
+// sectors instead of one sector per row, whatever the matrix ordering).  An
+// operand u_kq that no step updates keeps A's value throughout, so it is read
+// from A's values when the task starts and never awaited; only pivots and
+// updated u_kq are polled (for a 5- or 7-point stencil, only the pivots, and
+// lu then needs no sentinel fill).
+//
+// Reciprocal pivots (RCP, FP64 unless jv_options.exact_division): the pivot
+// a row publishes is y_k = 1/u_kk (Newton's iteration, rcp_newton), and a
+// dependant forms l_rk = a_rk * y_k.  On this part a warp instruction of the FP64 pipe costs
 // 64 cycles whatever its active lanes, and the three correctly rounded
 // divisions of a 7-point row were the longest run of FP64 work on the
 // critical path of every level; one reciprocal per row (five instructions)
@@ -80,8 +89,11 @@ struct FactorArgs {
     void *pscratch;               // operands of rows too long for shared memory
     long long npairs_total;       // offset of the u_kk area in pscratch
     const unsigned char *row_pull; // per row: take the pull form
-    const int *colidx;            // column of every entry (RCP: the pivot row k of entry (r, k))
-    void *rinv;                   // RCP: 1/u_kk of every row k (sentinel-filled in SYNCFREE mode)
+    const int *colidx;            // column of every entry: the pivot row k of entry (r, k)
+    const int *ppos;              // work-list position of every row (where its pivot is published)
+    const unsigned char *upd;     // 1: some step updates the entry (a pair operand to await)
+    void *piv;                    // pivot of every row at its work-list position: u_kk, or
+                                  // 1/u_kk with RCP (sentinel-filled in SYNCFREE mode)
 };
 
 template <class T> struct RN;
@@ -142,6 +154,16 @@ __device__ __forceinline__ void pivot_check(const FactorArgs &a, int r, T d) {
     if (Bits<T>::zero_or_nonfinite_bits(Bits<T>::to(d))) report(a.status, JV_ERR_ZERO_PIVOT, r);
 }
 
+// u_kq at lu position q: from A's values when no step updates it, else
+// awaited (bounded) on its own word.
+template <class TV, class TL, bool SF>
+__device__ __forceinline__ TL pair_operand(const FactorArgs &a, int q, int r, bool &fail) {
+    if (!__ldg(a.upd + q)) return (TL)__ldg(static_cast<const TV *>(a.vals) + q);
+    const TL *src = static_cast<const TL *>(a.lu) + q;
+    return Bits<TL>::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail)
+                             : first_read<TL, SF>(src));
+}
+
 // ------------------------------------------------------- one lane per row
 template <class TV, class TL, bool SF, int W, int S, bool RCP>
 __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi, unsigned gate,
@@ -161,10 +183,12 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     bool done = pos >= hi;
     int r = 0, rs = 0, len = 0, nl = 0, m = 0, got = 0;
     unsigned tmask = 0;                 // row-local entries some step of the row updates
+    unsigned smask = 0;                 // operands final from the start (read from A's values)
     TL *lu = static_cast<TL *>(a.lu);
-    TL *rinv = static_cast<TL *>(a.rinv);
-    // operand e of the row: y_k (RCP) or u_kk for a step, u_kq for a pair
-    auto src = [&](int e, int pos_) -> const TL * { return (RCP && e < nl ? rinv : lu) + pos_; };
+    TL *piv = static_cast<TL *>(a.piv);
+    // where operand e of the row is awaited: the pivot of a step (in piv, at
+    // the pivot row's work-list position), or u_kq of a pair (in lu)
+    auto src = [&](int e, int pos_) -> const TL * { return (e < nl ? piv : lu) + pos_; };
     if (!done) {
         r = __ldg(a.rows + pos);
         rs = __ldg(a.rowptr + r);
@@ -180,10 +204,20 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 #pragma unroll
         for (int e = 0; e < S; ++e) {
             if (e < len) v[e] = (TL)__ldg(vals + rs + e);
-            if (e < nl) kd[e] = RCP ? __ldg(a.colidx + rs + e) : __ldg(a.kdiag + rs + e);
+            if (e < nl) kd[e] = __ldg(a.colidx + rs + e);
             if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
             if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
         }
+        unsigned char up[S];
+        TL sv[S];
+#pragma unroll
+        for (int e = 0; e < S; ++e) {
+            if (e < nl) kd[e] = __ldg(a.ppos + kd[e]);             // pivot row -> its position
+            if (e < np) up[e] = __ldg(a.upd + pr[e].y);
+        }
+#pragma unroll
+        for (int e = 0; e < S; ++e)
+            if (e < np && !up[e]) sv[e] = (TL)__ldg(vals + pr[e].y);  // u_kq = a_kq throughout
 #pragma unroll
         for (int e = 0; e < S; ++e) {
             if (e < len) V(e) = v[e];
@@ -192,23 +226,23 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                 OPOS(nl + e) = pr[e].y;
                 TGT(e) = (unsigned char)(pr[e].x - rs);
                 tmask |= 1u << (pr[e].x - rs);
+                if (!up[e]) {
+                    V(len + nl + e) = sv[e];
+                    smask |= 1u << (nl + e);
+                }
             }
         }
-        // a U entry no step updates is final already: publish it now, so that
+        // a U entry no step updates is final already: store it now, so that
         // only the updated ones (for a stencil, the diagonal) follow the steps
-        if (!SF || r != a.fault_row) {
+        // (no row awaits it: a reader takes it from A's values)
 #pragma unroll
-            for (int e = 0; e < S; ++e)
-                if (e >= nl && e < len && !((tmask >> e) & 1u)) {
-                    if (SF) publish<TL>(lu + rs + e, v[e]);
-                    else lu[rs + e] = v[e];
-                }
-        }
-        if (SF && gate) {               // bring the operands' lines into L2 before sleeping
+        for (int e = 0; e < S; ++e)
+            if (e >= nl && e < len && !((tmask >> e) & 1u)) lu[rs + e] = v[e];
+        if (SF && gate) {               // bring the awaited operands' lines into L2 before sleeping
 #pragma unroll
             for (int e = 0; e < S; ++e) {
-                if (e < nl) prefetch_l2(src(e, kd[e]));
-                if (e < np) prefetch_l2(lu + pr[e].y);
+                if (e < nl) prefetch_l2(piv + kd[e]);
+                if (e < np && up[e]) prefetch_l2(lu + pr[e].y);
             }
         }
     }
@@ -224,19 +258,17 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             }
             V(p) = lik;
         }
-        // the updated U entries, the diagonal first, then (RCP) the pivot's
-        // reciprocal, then the L part
+        // the pivot (its reciprocal with RCP) first: the word the dependants
+        // of a stencil row wait on; then the updated U entries, then the L part
         if (!SF || r != a.fault_row) {
+            const TL pv = RCP ? rcp_newton(V(nl)) : V(nl);
+            if (SF) publish<TL>(piv + pos, pv);
+            else piv[pos] = pv;
             for (int e = nl; e < len; ++e)
                 if ((tmask >> e) & 1u) {
                     if (SF) publish<TL>(lu + rs + e, V(e));
                     else lu[rs + e] = V(e);
                 }
-            if constexpr (RCP) {
-                const TL y = rcp_newton(V(nl));
-                if (SF) publish<TL>(rinv + r, y);
-                else rinv[r] = y;
-            }
         }
         pivot_check<TL>(a, r, V(nl));
         for (int e = 0; e < nl; ++e) lu[rs + e] = V(e);
@@ -251,7 +283,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         int op[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) op[k] = k < m ? OPOS(k) : 0;
-        unsigned seen = 0u;
+        unsigned seen = smask;
         const unsigned need = (1u << m) - 1u;
         while (__any_sync(0xffffffffu, !done)) {
 #pragma unroll
@@ -299,17 +331,19 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                 wb = got;
                 wend = min(got + W, m);
             }
-            // (re-)read every operand of the window not taken yet; they tend to be
-            // published together, so they are all polled in the same round
+            // (re-)read every awaited operand of the window not taken yet; they
+            // tend to be published together, so they are all polled in the same round
 #pragma unroll
             for (int k = 0; k < W; ++k)
-                if (wb + k >= got && wb + k < wend) u[k] = first_read<TL, SF>(src(wb + k, OPOS(wb + k)));
+                if (wb + k >= got && wb + k < wend && !((smask >> (wb + k)) & 1u))
+                    u[k] = first_read<TL, SF>(src(wb + k, OPOS(wb + k)));
             bool ok = true;
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 if (wb + k < got) continue;
-                if (ok && wb + k < wend && (!SF || u[k] != B::kSent)) {
-                    V(len + wb + k) = B::from(u[k]);
+                const bool fixed = (smask >> (wb + k)) & 1u;     // already in V
+                if (ok && wb + k < wend && (fixed || !SF || u[k] != B::kSent)) {
+                    if (!fixed) V(len + wb + k) = B::from(u[k]);
                     ++got;
                 } else {
                     ok = false;
@@ -356,7 +390,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     const int m = nl + np;
     bool fail = false;                 // a wait gave up: publish nothing
     TL *lu = static_cast<TL *>(a.lu);
-    TL *rinv = static_cast<TL *>(a.rinv);
+    TL *piv = static_cast<TL *>(a.piv);
     const TV *vals = static_cast<const TV *>(a.vals);
     const size_t need = (size_t)(len + m) * sizeof(TL) + (size_t)(np + nl) * sizeof(int);
     const bool fast = need <= (size_t)warp_smem<S>();
@@ -377,16 +411,25 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
                 const int e = e0 + k * kWarp + lane;
                 src[k] = -1;
                 if (e < m) {
-                    src[k] = e < nl ? (RCP ? __ldg(a.colidx + rs + e) : __ldg(a.kdiag + rs + e))
-                                    : __ldg(a.pairs + j0 + e - nl).y;
-                    u[k] = first_read<TL, SF>((RCP && e < nl ? rinv : lu) + src[k]);
+                    if (e < nl) {                                  // the pivot of step e
+                        src[k] = __ldg(a.ppos + __ldg(a.colidx + rs + e));
+                        u[k] = first_read<TL, SF>(piv + src[k]);
+                    } else {                                       // u_kq of pair e - nl
+                        src[k] = __ldg(a.pairs + j0 + e - nl).y;
+                        if (__ldg(a.upd + src[k])) {
+                            u[k] = first_read<TL, SF>(lu + src[k]);
+                        } else {                                   // final from the start
+                            u[k] = B::to((TL)__ldg(vals + src[k]));
+                            src[k] = -2;
+                        }
+                    }
                 }
             }
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k)
-                if (src[k] >= 0) {
+                if (src[k] != -1) {
                     const int e = e0 + k * kWarp + lane;
-                    if (SF) u[k] = settle<TL>((RCP && e < nl ? rinv : lu) + src[k], u[k], a, r, fail);
+                    if (SF && src[k] >= 0) u[k] = settle<TL>((e < nl ? piv : lu) + src[k], u[k], a, r, fail);
                     uv[e] = B::from(u[k]);
                 }
         }
@@ -398,7 +441,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         if (fast) {
             ukk = uv[p];
         } else {
-            const TL *src = RCP ? rinv + __ldg(a.colidx + rs + p) : lu + __ldg(a.kdiag + rs + p);
+            const TL *src = piv + __ldg(a.ppos + __ldg(a.colidx + rs + p));
             ukk = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
         }
         const TL lik = RCP ? w[p] * ukk : RN<TL>::div(w[p], ukk);
@@ -414,8 +457,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
             } else {
                 const int2 tq = __ldg(a.pairs + j0 + j);
                 t = tq.x - rs;
-                const TL *src = lu + tq.y;
-                uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
+                uq = pair_operand<TV, TL, SF>(a, tq.y, r, fail);
             }
             if (!a.milu || t != nl) w[t] = RN<TL>::fms(lik, uq, w[t]);
         }
@@ -430,8 +472,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
                     const int2 tq = __ldg(a.pairs + j0 + j);
                     t = tq.x - rs;
                     if (t != nl) continue;
-                    const TL *src = lu + tq.y;
-                    uq = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
+                    uq = pair_operand<TV, TL, SF>(a, tq.y, r, fail);
                 }
                 if (t == nl) w[nl] = RN<TL>::fms(lik, uq, w[nl]);
             }
@@ -443,10 +484,10 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     __syncwarp();
     if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) pivot_check<TL>(a, r, w[nl]);
-    if (RCP && lane == 0 && (!SF || r != a.fault_row)) {
-        const TL y = rcp_newton(w[nl]);
-        if (SF) publish<TL>(rinv + r, y);
-        else rinv[r] = y;
+    if (lane == 0 && (!SF || r != a.fault_row)) {
+        const TL pv = RCP ? rcp_newton(w[nl]) : w[nl];
+        if (SF) publish<TL>(piv + pos, pv);
+        else piv[pos] = pv;
     }
     for (int e = lane; e < len; e += kWarp) {
         const TL v = w[e];
@@ -493,15 +534,12 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     }
     for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
-    TL *rinv = static_cast<TL *>(a.rinv);
+    TL *piv = static_cast<TL *>(a.piv);
     for (int e = lane; e < nl; e += kWarp) {               // u_kk, or its reciprocal (RCP)
-        const TL *src = RCP ? rinv + __ldg(a.colidx + rs + e) : lu + __ldg(a.kdiag + rs + e);
+        const TL *src = piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
         ukk[e] = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
     }
-    for (int e = lane; e < nq; e += kWarp) {
-        const TL *src = lu + __ldg(a.tpairs + s0 + e).y;
-        uq[e] = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
-    }
+    for (int e = lane; e < nq; e += kWarp) uq[e] = pair_operand<TV, TL, SF>(a, __ldg(a.tpairs + s0 + e).y, r, fail);
     __syncwarp();
     // L entries: chunks of 32, waves inside a chunk
     for (int c0 = 0; c0 < nl; c0 += kWarp) {
@@ -540,10 +578,10 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     __syncwarp();
     if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) pivot_check<TL>(a, r, w[nl]);
-    if (RCP && lane == 0 && (!SF || r != a.fault_row)) {
-        const TL y = rcp_newton(w[nl]);
-        if (SF) publish<TL>(rinv + r, y);
-        else rinv[r] = y;
+    if (lane == 0 && (!SF || r != a.fault_row)) {
+        const TL pv = RCP ? rcp_newton(w[nl]) : w[nl];
+        if (SF) publish<TL>(piv + pos, pv);
+        else piv[pos] = pv;
     }
     for (int e = lane; e < len; e += kWarp) {
         const TL v = w[e];
@@ -623,9 +661,9 @@ int launch_r(int window, int slot, int grid, cudaStream_t s, const FactorArgs &a
 }
 // reciprocal pivots for an FP64 factor unless exact division is asked for
 template <class TV, class TL, bool SF>
-int launch(int window, int slot, int grid, cudaStream_t s, const FactorArgs &a) {
+int launch(bool rcp, int window, int slot, int grid, cudaStream_t s, const FactorArgs &a) {
     if constexpr (sizeof(TL) == 8) {
-        if (a.rinv) return launch_r<TV, TL, SF, true>(window, slot, grid, s, a);
+        if (rcp) return launch_r<TV, TL, SF, true>(window, slot, grid, s, a);
     }
     return launch_r<TV, TL, SF, false>(window, slot, grid, s, a);
 }
@@ -659,19 +697,19 @@ int run(jv_handle h, const void *vals, void *lu) {
     }
     // reciprocal pivots: FP64 factors unless exact division is asked for
     const bool rcp = sizeof(TL) == 8 && !h->opt.exact_division;
-    if (rcp && h->rinv_bytes < (size_t)h->n * sizeof(TL)) {
-        if (h->rinv) {
+    if (h->piv_bytes < (size_t)h->n * sizeof(TL)) {          // the pivot array
+        if (h->piv) {
             JV_CUDA(cudaStreamSynchronize(s));
-            cudaFree(h->rinv);
-            h->rinv = nullptr;
-            h->rinv_bytes = 0;
+            cudaFree(h->piv);
+            h->piv = nullptr;
+            h->piv_bytes = 0;
         }
-        if (cudaMalloc(&h->rinv, (size_t)h->n * sizeof(TL) + 16) != cudaSuccess) {
+        if (cudaMalloc(&h->piv, (size_t)h->n * sizeof(double) + 16) != cudaSuccess) {
             cudaGetLastError();
-            h->rinv = nullptr;
+            h->piv = nullptr;
             return JV_ERR_NOMEM;
         }
-        h->rinv_bytes = (size_t)h->n * sizeof(TL);
+        h->piv_bytes = (size_t)h->n * sizeof(double);
     }
     const void *const user_vals = vals;
     void *const copy = inplace ? static_cast<char *>(h->fscratch) + (size_t)h->nnz * sizeof(double)
@@ -715,7 +753,9 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.npairs_total = h->npairs;
     a.row_pull = h->row_pull;
     a.colidx = h->colidx;
-    a.rinv = rcp ? h->rinv : nullptr;
+    a.ppos = W.ipos;
+    a.upd = h->upd;
+    a.piv = h->piv;
     a.backoff_ns = sf_backoff(h);
     // the upper stage: levels [0, lend), above the Even-Rows corner if any
     const jv_dtype lu_t = sizeof(TL) == 8 ? JV_F64 : JV_F32;
@@ -728,20 +768,23 @@ int run(jv_handle h, const void *vals, void *lu) {
         auto one_level = [&](int l) {
             a.task_begin = W.h_task_ptr[l];
             a.task_end = W.h_task_ptr[l + 1];
-            return launch<TV, TL, false>(W.window, h->fslot,
+            return launch<TV, TL, false>(rcp, W.window, h->fslot,
                                          grid_for(a.task_end - a.task_begin, kWarpsPerBlock), s, a);
         };
         auto sync_free = [&](int l0, int l1) {
             a.task_begin = W.h_task_ptr[l0];
             a.task_end = W.h_task_ptr[l1];
             if (a.task_end <= a.task_begin) return (int)JV_OK;
-            return launch<TV, TL, true>(W.window, h->fslot, sf_grid(h, a.task_end - a.task_begin), s, a);
+            return launch<TV, TL, true>(rcp, W.window, h->fslot, sf_grid(h, a.task_end - a.task_begin), s, a);
         };
         int rc = JV_OK;
         if (has_sync_free(h, L, lend)) {
-            rc = rcp ? fill2_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, h->rinv,
-                                 (size_t)h->n * sizeof(TL) / 4, ~0u, s)
-                     : fill_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, ~0u, s);
+            // the awaited words carry the sentinel until they are published:
+            // every pivot, and lu too when some pair operand is an entry the
+            // steps update (none for the 5- and 7-point stencils)
+            rc = h->ndyn_pairs > 0 ? fill2_u32(lu, (size_t)h->nnz * sizeof(TL) / 4, h->piv,
+                                               (size_t)h->n * sizeof(TL) / 4, ~0u, s)
+                                   : fill_u32(h->piv, (size_t)h->n * sizeof(TL) / 4, ~0u, s);
             if (rc) return rc;
         }
         if (h->opt.mode == JV_MODE_SYNCFREE) {
@@ -764,7 +807,7 @@ int run(jv_handle h, const void *vals, void *lu) {
     const std::vector<unsigned long long> key = {
         1, sizeof(TV), sizeof(TL), (unsigned long long)h->opt.mode, (unsigned long long)(uintptr_t)user_vals,
         (unsigned long long)(uintptr_t)lu, (unsigned long long)(uintptr_t)h->fscratch,
-        (unsigned long long)(uintptr_t)h->pscratch, (unsigned long long)(uintptr_t)a.rinv};
+        (unsigned long long)(uintptr_t)h->pscratch, (unsigned long long)(uintptr_t)h->piv};
     return graph_run(h, key, seq);
 }
 

@@ -269,6 +269,21 @@ __device__ __forceinline__ double rcp_newton(double d) {
     return __fma_rn(y, e, y);
 }
 
+// s / d from y = rcp_newton(d): q = s y, then one correction with the exact
+// residual, q + (s - d q) y (Markstein's method: with y the correctly
+// rounded 1/d, the corrected quotient is the correctly rounded s / d).
+// Three FP64-pipe instructions once y is known, against about ten for a
+// division.  Inputs with exponents outside +-500 (where q or the residual
+// could overflow or underflow), and zero s (whose sign the correction can
+// lose), take __ddiv_rn.
+__device__ __forceinline__ double div_rcp(double s, double d, double y) {
+    const unsigned es = (unsigned)((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ffu;
+    const unsigned ed = (unsigned)((unsigned long long)__double_as_longlong(d) >> 52) & 0x7ffu;
+    if (es - 523u > 1000u || ed - 523u > 1000u) return __ddiv_rn(s, d);
+    const double q = s * y;
+    return __fma_rn(__fma_rn(-d, q, s), y, q);
+}
+
 // f(i) = a[i + ai] + ad: one kernel can walk a CSR or CSC sub-range of row or
 // column i (e.g. the strictly lower part of row i is [rowptr[i], diag[i])).
 struct Span {
@@ -297,6 +312,7 @@ __device__ __forceinline__ int find_col(const int *__restrict__ col, int lo, int
 constexpr int kLongBit = (int)0x80000000u;   // task_hi flag: one-row cooperative task
 struct Bins {
     int *rows = nullptr;       // [n] binned rows
+    int *ipos = nullptr;       // [n] position of every row in rows (inverse of rows)
     int *task_lo = nullptr;    // [ntasks] first position in rows
     int *task_hi = nullptr;    // [ntasks] end position, | kLongBit for a long-row task
     int *task_lev = nullptr;   // [ntasks] level of every task
@@ -425,6 +441,8 @@ struct jv_handle_s {
     int *tpair_ptr = nullptr;                // [nnz + 1] the pairs grouped by target entry t:
     int2 *tpairs = nullptr;                  // [npairs] (p, q) -- step p, operand q -- ascending p
     unsigned char *row_pull = nullptr;       // [n] 1: a one-warp row takes the pull form
+    unsigned char *upd = nullptr;            // [nnz] 1: some step of the factor updates the entry
+    long long ndyn_pairs = 0;                // pairs whose operand is updated (must be awaited)
     long long npairs = 0;
     jv::Bins fbins;                          // factor work list over the levels of lower(A)
     jv::CornerPlan corner[2];                // Even-Rows corner per factor dtype (jv_dtype)
@@ -439,8 +457,10 @@ struct jv_handle_s {
     void *xscratch = nullptr;                // FP32 solution of FP32-factor solves into FP64 x
     size_t xscratch_bytes = 0;
     void *pscratch = nullptr;                // operands of long rows: [npairs + nnz] elements
-    void *rinv = nullptr;                    // FP64 factor: 1/u_kk of every row, published by
-    size_t rinv_bytes = 0;                   // the row (sentinel-filled in sync-free mode)
+    void *piv = nullptr;                     // factor: the pivot of every row (u_kk, or 1/u_kk
+    size_t piv_bytes = 0;                    // with reciprocal pivots), published by the row at
+                                             // its factor work-list position (sentinel-filled in
+                                             // sync-free mode)
     int fslot = jv::kLaneSlot;               // factor one-lane slot (kLaneSlot or kLaneSlotWide)
     size_t pscratch_bytes = 0;
     // scratch shared by the sync-free kernels

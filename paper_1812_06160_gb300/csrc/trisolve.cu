@@ -9,8 +9,10 @@
 // csc2csr).  The order is the one the serial substitution uses (ascending
 // columns; descending rows for L^T) and every update is one fused
 // multiply-add, so the result equals the serial solve bit for bit; only the
-// loads run in parallel.  (FP64 U and U^T solves multiply by 1/u_rr unless
-// jv_options.exact_division asks for the division: see TriArgs::rcp.)
+// loads run in parallel.  (FP64 U and U^T solves form s / u_rr from 1/u_rr,
+// computed while the row waits, and one correction -- the same quotient as
+// the division, with a third of its instructions after the last operand
+// arrives -- unless jv_options.exact_division asks for the division itself.)
 //
 // Work list (see Bins): a short task holds up to 32 rows of one level, one
 // lane per row.  Every lane polls the next W dependencies of its own row (a
@@ -42,8 +44,8 @@ struct TriArgs {
     const int *vmap;       // CSC -> CSR value position, or nullptr
     const int *diag;
     int unit;              // 1: unit diagonal (L, L^T)
-    int rcp;               // FP64 U, U^T: multiply by 1/u_rr (rcp_newton, computed before the
-                           // row's operands arrive) instead of dividing by u_rr
+    int rcp;               // FP64 U, U^T: divide through 1/u_rr (rcp_newton, computed before
+                           // the row's operands arrive) and one correction (div_rcp)
     int reverse;           // 1: walk the range from its end (L^T)
     const int *rows, *task_lo, *task_hi;
     int task_begin, task_end;
@@ -116,21 +118,23 @@ __device__ __forceinline__ TL load_val(const TriArgs &a, int q) {
     return a.vmap ? __ldg(lu + __ldg(a.vmap + q)) : __ldg(lu + q);
 }
 
-// The diagonal a row finishes with: u_rr, or 1/u_rr when the solve multiplies.
+// The diagonal a row finishes with, u_rr, and (FP64 with rcp) its reciprocal
+// y, computed while the row waits for its operands.
 template <class TL>
-__device__ __forceinline__ TL load_diag(const TriArgs &a, int r) {
+__device__ __forceinline__ TL load_diag(const TriArgs &a, int r, TL &y) {
     const TL d = __ldg(static_cast<const TL *>(a.lu) + __ldg(a.diag + r));
+    y = (TL)1;
     if constexpr (sizeof(TL) == 8) {
-        if (a.rcp) return rcp_newton(d);
+        if (a.rcp) y = rcp_newton(d);
     }
     return d;
 }
-// x_r from the finished sum s and load_diag's d
+// x_r = s / u_rr from the finished sum (the same quotient either way)
 template <class TL>
-__device__ __forceinline__ TL finish_row(const TriArgs &a, TL s, TL d) {
+__device__ __forceinline__ TL finish_row(const TriArgs &a, TL s, TL d, TL y) {
     if (a.unit) return s;
     if constexpr (sizeof(TL) == 8) {
-        if (a.rcp) return s * d;
+        if (a.rcp) return div_rcp(s, d, y);
     }
     return RN<TL>::div(s, d);
 }
@@ -156,7 +160,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     TX *x = static_cast<TX *>(a.x);
     bool done = pos >= hi;
     int r = 0, qb = 0, len = 0, e = 0, wb = 0, wend = 0;
-    TL s = 0, d = 1;
+    TL s = 0, d = 1, dy = 1;
     int jw[W];
     TL vw[W];
     if (!done) {
@@ -164,7 +168,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
         qb = a.beg.at(r);
         len = a.end.at(r) - qb;
         s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
-        if (!a.unit) d = load_diag<TL>(a, r);
+        if (!a.unit) d = load_diag<TL>(a, r, dy);
         if (len > 0) {               // first window: indices and values
             wend = min(W, len);
 #pragma unroll
@@ -223,7 +227,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
 #pragma unroll
                 for (int k = 0; k < W; ++k)
                     if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
-                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
+                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
             }
             return;
         }
@@ -252,7 +256,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                     for (int k = 0; k < W; ++k)
                         if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
                 }
-                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
+                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
                 done = true;
             } else if (!done) {
                 if (rounds++ == 0) t0 = clock64();
@@ -309,7 +313,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                 }
             }
             if (e == len) {
-                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
+                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
                 done = true;
             }
         }
@@ -340,7 +344,8 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     const int qb = a.beg.at(r);
     const int len = a.end.at(r) - qb;
     TL s = (TL)__ldg(static_cast<const TB *>(a.b) + r);
-    const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r);
+    TL dy = 1;
+    const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r, dy);
     bool fail = false;                 // a wait gave up: publish nothing
     for (int c0 = 0; c0 < len; c0 += CH) {
         int q[kUnroll];
@@ -377,7 +382,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
             }
     }
     if (SF && __any_sync(0xffffffffu, fail)) return;
-    if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d));
+    if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
 }
 
 template <class TL, class TB, class TX, bool SF, int W, bool ONE>
@@ -411,7 +416,8 @@ __device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
     const size_t ld = (size_t)a.nrhs;
     TX *x = static_cast<TX *>(a.x);
     const TB *b = static_cast<const TB *>(a.b);
-    const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r);
+    TL dy = 1;
+    const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r, dy);
     for (int c0 = 0; c0 < a.nrhs; c0 += 32) {
         const int c = c0 + lane;
         const bool ok = c < a.nrhs;
@@ -442,7 +448,7 @@ __device__ __forceinline__ void trsm_task(const TriArgs &a, int task) {
                 }
             }
         }
-        if (ok && !fail) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, finish_row<TL>(a, s, d));
+        if (ok && !fail) store_x<TL, TX>(a, SF, x + (size_t)r * ld + c, r, finish_row<TL>(a, s, d, dy));
     }
 }
 

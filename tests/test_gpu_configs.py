@@ -77,10 +77,16 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False, exact=False
             assert np.array_equal(y.cpu().numpy(), oy)
             assert np.array_equal(z.cpu().numpy(), oz)
         else:
+            # against the oracle's pipeline (its own factor): within 1e-12
             for name, got, want in (("lsolve", y, oy), ("usolve", z, oz)):
                 ok, err = close(got.cpu().numpy(), want)
                 print(f"{name}: largest relative error {err:.2e}")
                 assert ok, (name, err)
+            # and on the GPU's factor the solves are the serial ones bit for bit
+            glu = lu.cpu().numpy()
+            gy = O.lsolve(rp, ci, diag, glu, bb)
+            assert np.array_equal(y.cpu().numpy(), gy)
+            assert np.array_equal(z.cpu().numpy(), O.usolve(rp, ci, diag, glu, gy))
         x = W.rhs(len(rp) - 1, 1, seed=21)
         s = jv.jv_spmv(h, T(v), T(x)).cpu().numpy()
         assert np.array_equal(s, O.spmv(rp, ci, v, x))

@@ -54,8 +54,9 @@ def test_factor_fp64_reciprocal_pivots_within_1e12(case, mode):
 @pytest.mark.parametrize("nrhs", [1, 3, 33])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_solves_fp64_reciprocal_diagonal(case, nrhs, mode):
-    # default mode: the L and L^T solves (no division) stay bit-exact; the U
-    # and U^T solves multiply by 1/u_ii and stay within 1e-12 relative
+    # default mode: the U and U^T solves form s / u_ii from 1/u_ii and one
+    # correction step, which gives the division's own result: all four
+    # solves stay bit-exact
     _, rp, ci, v = case
     n = len(rp) - 1
     h = analyze(jv, rp, ci, mode, exact_division=False)
@@ -63,15 +64,11 @@ def test_solves_fp64_reciprocal_diagonal(case, nrhs, mode):
     diag = O.diag_ptr(rp, ci)
     b = W.rhs(n, nrhs, seed=17 + nrhs)
     lu, bt = T(olu), T(b)
-    for name, ofn, exact in (("jv_lsolve", O.lsolve, True), ("jv_usolve", O.usolve, False),
-                             ("jv_lsolve_t", O.lsolve_t, True), ("jv_usolve_t", O.usolve_t, False)):
+    for name, ofn in (("jv_lsolve", O.lsolve), ("jv_usolve", O.usolve),
+                      ("jv_lsolve_t", O.lsolve_t), ("jv_usolve_t", O.usolve_t)):
         x = getattr(jv, name)(h, lu, bt).cpu().numpy()
         want = ofn(rp, ci, diag, olu, b)
-        if exact:
-            assert np.array_equal(x, want), (name, close(x, want)[1])
-        else:
-            ok, err = close(x, want)
-            assert ok, (name, err)
+        assert np.array_equal(x, want), (name, close(x, want)[1])
 
 
 @pytest.mark.parametrize("mode", MODES)
