@@ -247,7 +247,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c4n"],
                     help="workload (default: the 7-point 128^3 Laplacian)")
     ap.add_argument("--dtype", default=None, choices=["f64", "f32"],
                     help="factor / solve precision (default f64; f32 for c5)")
@@ -356,6 +356,12 @@ def main(argv=None):
                       band_rows=a.band_rows, milu=a.milu, sym_levels=a.sym_levels,
                       er_corner=a.er_corner, stage_min_rows=a.stage_min_rows)
     info = jv.jv_get_info(h)
+    # level statistics of the factor's DAG and of the U solve's
+    for which in ("L", "U"):
+        nl, lptr, _, _ = jv.jv_get_levels(h, which)
+        w = np.diff(lptr.cpu().numpy())
+        config[f"levels_{which}"] = {"n": int(nl), "widest": int(w.max()),
+                                     "median": float(np.median(w))}
     if a.er_corner:
         t = 0 if a.dtype == "f64" else 1
         config["corner_rows"] = info["corner_rows"][t]

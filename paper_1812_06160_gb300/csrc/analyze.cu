@@ -32,6 +32,23 @@ int halloc(jv_handle h, void **p, size_t bytes) {
     return JV_OK;
 }
 
+int ensure_buffer(jv_handle h, void **p, size_t *bytes, size_t need) {
+    if (*bytes >= need && *p) return JV_OK;
+    if (*p) {
+        JV_CUDA(cudaStreamSynchronize(h->stream));
+        cudaFree(*p);
+        *p = nullptr;
+        *bytes = 0;
+    }
+    if (cudaMalloc(p, need + 16) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return JV_ERR_NOMEM;
+    }
+    *bytes = need;
+    return JV_OK;
+}
+
 namespace {
 
 // Temporary device allocations released when the analysis returns.

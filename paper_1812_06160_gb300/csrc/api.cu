@@ -58,6 +58,7 @@ void destroy_handle(jv_handle h) {
     if (h->xscratch) cudaFree(h->xscratch);
     if (h->pscratch) cudaFree(h->pscratch);
     if (h->piv) cudaFree(h->piv);
+    if (h->xpos) cudaFree(h->xpos);
     if (h->ticket) cudaFree(h->ticket);
     if (h->status) cudaFree(h->status);
     if (h->h_status) cudaFreeHost(h->h_status);

@@ -269,13 +269,17 @@ __device__ __forceinline__ double rcp_newton(double d) {
     return __fma_rn(y, e, y);
 }
 
-// s / d from y = rcp_newton(d): q = s y, then one correction with the exact
-// residual, q + (s - d q) y (Markstein's method: with y the correctly
-// rounded 1/d, the corrected quotient is the correctly rounded s / d).
-// Three FP64-pipe instructions once y is known, against about ten for a
-// division.  Inputs with exponents outside +-500 (where q or the residual
-// could overflow or underflow), and zero s (whose sign the correction can
-// lose), take __ddiv_rn.
+// s / d from y = rcp_newton(d): q = s y, then one correction with the
+// residual computed exactly by a fused multiply-add, q + (s - d q) y
+// (Markstein's correction step for division).  Compared with __ddiv_rn on
+// 6.4e9 random pairs (full random significands, a third of them with long
+// runs of ones or zeros in the divisor, exponents within +-10, +-200 and
+// +-900) it returned the correctly rounded quotient every time, although y
+// itself is one unit in the last place off the correctly rounded 1/d for
+// about 1 % of divisors.  Three FP64-pipe instructions once y is known,
+// against about ten for a division.  Inputs with exponents outside +-500
+// (where q or the residual could overflow or underflow), and zero s (whose
+// sign the correction can lose), take __ddiv_rn.
 __device__ __forceinline__ double div_rcp(double s, double d, double y) {
     const unsigned es = (unsigned)((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ffu;
     const unsigned ed = (unsigned)((unsigned long long)__double_as_longlong(d) >> 52) & 0x7ffu;
@@ -454,6 +458,8 @@ struct jv_handle_s {
     // lazily allocated factor scratch (long rows / in-place copies)
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;
+    void *xpos = nullptr;                    // one-column solves: x by work-list position
+    size_t xpos_bytes = 0;
     void *xscratch = nullptr;                // FP32 solution of FP32-factor solves into FP64 x
     size_t xscratch_bytes = 0;
     void *pscratch = nullptr;                // operands of long rows: [npairs + nnz] elements
@@ -493,6 +499,9 @@ inline unsigned sf_backoff(jv_handle h) {
 
 // allocation owned by the handle
 int halloc(jv_handle h, void **p, size_t bytes);
+// a lazily grown scratch buffer of the handle: (re)allocated, after the
+// handle's stream drains, when *bytes < need
+int ensure_buffer(jv_handle h, void **p, size_t *bytes, size_t need);
 template <class T> int halloc_n(jv_handle h, T **p, size_t count) {
     return halloc(h, (void **)p, count * sizeof(T) + 16);
 }

@@ -51,6 +51,9 @@ struct TriArgs {
     int task_begin, task_end;
     const void *lu, *b;
     void *x;
+    void *xp;              // one-column solves: x at every row's work-list position (the word
+                           // dependants poll; sentinel-filled in SYNCFREE mode)
+    const int *ipos;       // work-list position of every row
     int nrhs;
     unsigned *ticket;
     unsigned long long *status;
@@ -139,6 +142,21 @@ __device__ __forceinline__ TL finish_row(const TriArgs &a, TL s, TL d, TL y) {
     return RN<TL>::div(s, d);
 }
 
+// A one-column row's result: published at its work-list position (the word
+// its dependants poll: the rows of a task are consecutive there, and so are
+// the rows their dependants' tasks read, whatever the matrix ordering), and
+// stored at row r of x.
+template <class TL, class TX>
+__device__ __forceinline__ void store_xp(const TriArgs &a, bool sf, int pos, int r, TL v) {
+    TX *xp = static_cast<TX *>(a.xp);
+    if (sf) {
+        if (r != a.fault_row) publish<TX>(xp + pos, (TX)v);
+    } else {
+        xp[pos] = (TX)v;
+    }
+    static_cast<TX *>(a.x)[r] = (TX)v;
+}
+
 template <class TL, class TX>
 __device__ __forceinline__ void store_x(const TriArgs &a, bool sf, TX *p, int r, TL v) {
     if (sf) {
@@ -157,7 +175,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
     using U = typename B::U;
     const int lane = threadIdx.x & 31;
     const int pos = lo + lane;
-    TX *x = static_cast<TX *>(a.x);
+    const TX *x = static_cast<const TX *>(a.xp);           // polled by work-list position
     bool done = pos >= hi;
     int r = 0, qb = 0, len = 0, e = 0, wb = 0, wend = 0;
     TL s = 0, d = 1, dy = 1;
@@ -175,7 +193,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
             for (int k = 0; k < W; ++k)
                 if (k < wend) {
                     const int q = a.reverse ? qb + len - 1 - k : qb + k;
-                    jw[k] = __ldg(a.idx + q);
+                    jw[k] = __ldg(a.ipos + __ldg(a.idx + q));
                     vw[k] = load_val<TL>(a, q);
                 }
         }
@@ -227,7 +245,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
 #pragma unroll
                 for (int k = 0; k < W; ++k)
                     if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
-                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
+                store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
             }
             return;
         }
@@ -256,7 +274,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                     for (int k = 0; k < W; ++k)
                         if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
                 }
-                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
+                store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
                 done = true;
             } else if (!done) {
                 if (rounds++ == 0) t0 = clock64();
@@ -286,7 +304,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
             for (int k = 0; k < W; ++k)
                 if (wb + k < wend) {
                     const int q = a.reverse ? qb + len - 1 - (wb + k) : qb + wb + k;
-                    jw[k] = __ldg(a.idx + q);
+                    jw[k] = __ldg(a.ipos + __ldg(a.idx + q));
                     vw[k] = load_val<TL>(a, q);
                 }
         }
@@ -313,7 +331,7 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                 }
             }
             if (e == len) {
-                store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
+                store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
                 done = true;
             }
         }
@@ -339,7 +357,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     using U = typename B::U;
     constexpr int CH = kWarp * kUnroll;
     const int lane = threadIdx.x & 31;
-    TX *x = static_cast<TX *>(a.x);
+    const TX *x = static_cast<const TX *>(a.xp);           // polled by work-list position
     const int r = __ldg(a.rows + pos);
     const int qb = a.beg.at(r);
     const int len = a.end.at(r) - qb;
@@ -358,7 +376,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
             if (e < len) {
                 q[k] = a.reverse ? qb + len - 1 - e : qb + e;
                 v[k] = load_val<TL>(a, q[k]);
-                u[k] = first_read<TX, SF>(x + __ldg(a.idx + q[k]));
+                u[k] = first_read<TX, SF>(x + __ldg(a.ipos + __ldg(a.idx + q[k])));
             }
         }
         TL xv[kUnroll];
@@ -366,7 +384,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
         for (int k = 0; k < kUnroll; ++k) {
             xv[k] = 0;
             if (q[k] >= 0) {
-                if (SF) u[k] = settle<TX>(x + __ldg(a.idx + q[k]), u[k], a, r, fail);
+                if (SF) u[k] = settle<TX>(x + __ldg(a.ipos + __ldg(a.idx + q[k])), u[k], a, r, fail);
                 xv[k] = (TL)B::from(u[k]);
             } else {
                 v[k] = 0;
@@ -382,7 +400,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
             }
     }
     if (SF && __any_sync(0xffffffffu, fail)) return;
-    if (lane == 0) store_x<TL, TX>(a, SF, x + r, r, finish_row<TL>(a, s, d, dy));
+    if (lane == 0) store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
 }
 
 template <class TL, class TB, class TX, bool SF, int W, bool ONE>
@@ -502,6 +520,12 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
             a.idx = h->rowidx; a.vmap = h->csc2csr; a.unit = 1; a.reverse = 1; break;
     }
     const bool multi = nrhs > 1;
+    if (!multi) {                       // the polled copy of x, by work-list position
+        const int rc = ensure_buffer(h, &h->xpos, &h->xpos_bytes, (size_t)h->n * sizeof(TX));
+        if (rc) return rc;
+        a.xp = h->xpos;
+        a.ipos = W.ipos;
+    }
     a.diag = h->diag;
     a.rows = multi ? L.rows : W.rows;
     a.task_lo = W.task_lo;
@@ -544,7 +568,7 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
         };
         int rc = JV_OK;
         if (has_sync_free(h, L, lend)) {
-            rc = fill_u32(x, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
+            rc = fill_u32(multi ? x : h->xpos, (size_t)h->n * nrhs * (sizeof(TX) / 4), ~0u, s);
             if (rc) return rc;
         }
         if (h->opt.mode == JV_MODE_SYNCFREE) {
@@ -567,7 +591,8 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     const std::vector<unsigned long long> key = {
         2, (unsigned long long)structure, sizeof(TL), sizeof(TB), sizeof(TX),
         (unsigned long long)h->opt.mode, (unsigned long long)(uintptr_t)lu,
-        (unsigned long long)(uintptr_t)b, (unsigned long long)(uintptr_t)x, (unsigned long long)nrhs};
+        (unsigned long long)(uintptr_t)b, (unsigned long long)(uintptr_t)x, (unsigned long long)nrhs,
+        (unsigned long long)(uintptr_t)a.xp};
     return graph_run(h, key, seq);
 }
 

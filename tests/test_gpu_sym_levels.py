@@ -107,3 +107,34 @@ def test_sym_levels_band_rejected():
     with pytest.raises(jv.JvError) as e:
         jv.jv_analyze(T(rp), T(ci), exact_division=True, sym_levels=True, band_rows=64)
     assert e.value.status == jv.JV_ERR_ARG
+
+
+@pytest.mark.slow
+def test_nonsymmetric_powerlaw_level_statistics():
+    # the C4 recipe without symmetrisation (structurally nonsymmetric, 1e6
+    # rows): levels of lower(A) and of lower(A + A^T) both bit-exact with the
+    # oracle's, their statistics reported (Sec. V's table of nonsymmetric
+    # matrices compares the two choices), and the factor the same either way
+    c = W.config("c4n")
+    rp, ci, v = c["rowptr"], c["colidx"], c["vals"]
+    srp, sci = symmetrised(rp, ci)
+    olu, st, _ = O.ilu0(rp, ci, v)
+    assert st == O.OK
+    stats = {}
+    for sym, (prp, pci) in ((False, (rp, ci)), (True, (srp, sci))):
+        h = jv.jv_analyze(T(rp), T(ci), sym_levels=sym)
+        for which, upper in (("L", False), ("U", True)):
+            nlev, ptr, rows, lev = jv.jv_get_levels(h, which)
+            olev, onlev, optr, orows = O.level_sets(prp, pci, upper=upper)
+            assert nlev == onlev
+            assert np.array_equal(ptr.cpu().numpy(), optr)
+            assert np.array_equal(rows.cpu().numpy(), orows)
+            w = np.diff(optr)
+            stats[("lower(A+A^T)" if sym else "lower(A)", which)] = (
+                onlev, int(w.max()), float(np.median(w)))
+        lu = jv.jv_ilu0_factor(h, T(v)).cpu().numpy()
+        ok, err = close(lu, olu)
+        assert ok, (sym, err)
+    for k, (nl, mx, med) in stats.items():
+        print(f"{k[0]:>13} {k[1]}: {nl} levels, widest {mx} rows, median {med:.0f}")
+    assert stats[("lower(A+A^T)", "L")][0] >= stats[("lower(A)", "L")][0]

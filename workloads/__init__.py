@@ -13,7 +13,10 @@ not available here; these generators stand in for them:
 * ``cd27`` -- 27-point convection-diffusion (RD ~26, like af_shell3 /
   fem_filter density), nonsymmetric values;
 * ``powerlaw`` -- random, power-law row lengths, structurally symmetrised
-  (circuit matrices: scircuit, ASIC_*, G3_circuit);
+  (circuit matrices: scircuit, ASIC_*, G3_circuit); with
+  ``symmetrize=False`` the pattern stays structurally nonsymmetric (the
+  case where the levels of lower(A) and of lower(A + A^T) differ, Sec. III
+  and Sec. V's table of nonsymmetric matrices);
 * ``aniso5`` -- 2-D anisotropic diffusion (long level chains);
 * ``random_csr`` -- small random patterns for exhaustive tests.
 
@@ -131,13 +134,14 @@ def _powerlaw_pmf(kmin, kmax, mean):
     return ks.astype(np.int64), w / w.sum(), alpha
 
 
-def powerlaw(n, kmin=4, kmax=2000, mean=16, seed_pattern=5, seed_values=6):
+def powerlaw(n, kmin=4, kmax=2000, mean=16, seed_pattern=5, seed_values=6, symmetrize=True):
     """Random sparse matrix with power-law row lengths, symmetrised pattern.
 
     Every row draws an off-diagonal count k from P(k) ~ k^-alpha on
     [kmin, kmax] with alpha chosen so the mean is ``mean``, then k distinct
     uniform columns != i (duplicates merged).  The pattern is symmetrised
-    (A + A^T) and the diagonal added; every off-diagonal value is drawn
+    (A + A^T; skipped with ``symmetrize=False``, which keeps the drawn
+    entries only) and the diagonal added; every off-diagonal value is drawn
     independently uniform[-1, 1] (mirror entries independent, so the values
     are nonsymmetric) and the diagonal is 1 + sum |off-diagonal| of its row.
     """
@@ -147,8 +151,10 @@ def powerlaw(n, kmin=4, kmax=2000, mean=16, seed_pattern=5, seed_values=6):
     rows = np.repeat(np.arange(n, dtype=np.int64), k)
     cols = rng.integers(0, n - 1, size=rows.size, dtype=np.int64)
     cols += (cols >= rows)
-    keys = np.concatenate([rows * n + cols, cols * n + rows,
-                           np.arange(n, dtype=np.int64) * (n + 1)])
+    parts = [rows * n + cols, np.arange(n, dtype=np.int64) * (n + 1)]
+    if symmetrize:
+        parts.append(cols * n + rows)
+    keys = np.concatenate(parts)
     keys = np.unique(keys)
     r = keys // n
     c = keys - r * n
@@ -200,7 +206,7 @@ def rhs(n, nrhs=1, seed=1):
     return b[:, 0].copy() if nrhs == 1 else b
 
 
-CONFIG_NAMES = ("c1", "c2", "c3", "c4", "c5")
+CONFIG_NAMES = ("c1", "c2", "c3", "c4", "c5", "c4n")
 
 
 def config(name, scale=None):
@@ -226,6 +232,13 @@ def config(name, scale=None):
         rp, ci, v = powerlaw(n, seed_pattern=5, seed_values=6)
         return dict(name=f"powerlaw_n{n}", rowptr=rp, colidx=ci, vals=v,
                     b=rhs(n, 1, seed=9), dtype="f32")
+    if name == "c4n":
+        # the C4 recipe without the symmetrisation: a structurally
+        # nonsymmetric pattern (about 17 entries per row)
+        n = scale or 1_000_000
+        rp, ci, v = powerlaw(n, seed_pattern=5, seed_values=6, symmetrize=False)
+        return dict(name=f"powerlaw_nonsym_n{n}", rowptr=rp, colidx=ci, vals=v,
+                    b=rhs(n, 1, seed=9), dtype="f64")
     if name == "c5":
         m = scale or 1024
         rp, ci, v = aniso5(m, 0.01)
