@@ -365,8 +365,10 @@ __global__ void k_row_costs(int n, const int *rowptr, const int *diag, const int
 
 // Host-side binning of one level structure (see Bins).
 // ops[r]: operands a one-lane row r awaits (sets the poll window).
+// group[r] (factor only, may be null): 1 when a row above the threshold is
+// run by kGroupLanes lanes, kWarp / kGroupLanes rows to a task.
 int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, const int *ops,
-              Bins &B) {
+              Bins &B, const unsigned char *group = nullptr) {
     const int n = h->n;
     cudaStream_t s = h->stream;
     std::vector<int> rows((size_t)n), brows, lo, hi;
@@ -378,6 +380,7 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
     const int per_task = (long long)n < 2048LL * L.nlev ? 16 : kWarp;
     B.h_task_ptr.assign(L.nlev + 1, 0);
     B.nlong = 0;
+    B.ngroup = 0;
     for (int l = 0; l < L.nlev; ++l) {
         B.h_task_ptr[l] = (int)lo.size();
         const int a = L.h_ptr[l], e = L.h_ptr[l + 1];
@@ -389,8 +392,19 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
             lo.push_back(first + t);
             hi.push_back(first + std::min(t + per_task, nshort));
         }
+        if (group) {
+            const int gfirst = (int)brows.size();
+            for (int t = a; t < e; ++t)
+                if (cost[rows[t]] > threshold && group[rows[t]]) brows.push_back(rows[t]);
+            const int ng = (int)brows.size() - gfirst;
+            for (int t = 0; t < ng; t += kWarp / kGroupLanes) {
+                lo.push_back(gfirst + t);
+                hi.push_back((gfirst + std::min(t + kWarp / kGroupLanes, ng)) | kGroupBit);
+                ++B.ngroup;
+            }
+        }
         for (int t = a; t < e; ++t)
-            if (cost[rows[t]] > threshold) {
+            if (cost[rows[t]] > threshold && !(group && group[rows[t]])) {
                 lo.push_back((int)brows.size());
                 hi.push_back(((int)brows.size() + 1) | kLongBit);
                 brows.push_back(rows[t]);
@@ -401,7 +415,7 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
     B.h_task_ptr[L.nlev] = B.ntasks;
     int most = 0;
     for (int t = 0; t < B.ntasks; ++t)
-        if (!(hi[t] & kLongBit))
+        if (!(hi[t] & (kLongBit | kGroupBit)))
             for (int p = lo[t]; p < hi[t]; ++p) most = std::max(most, ops[brows[p]]);
     // > 16: some row needs several windows of kPoll (the general poll loop)
     B.window = most <= 2 ? 2 : most <= 4 ? 4 : most <= 8 ? 8 : most <= 16 ? 16 : 17;
@@ -607,23 +621,21 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
         JV_CUDA(cudaStreamSynchronize(s));
     }
 
-    // spmv row blocks (greedy over the host copy of rowptr) and the longest row
+    // spmv: rows by length, longest first (a stable counting sort), and the longest row
     std::vector<int> hrp((size_t)n + 1);
     JV_CUDA(cudaMemcpyAsync(hrp.data(), h->rowptr, hrp.size() * 4, cudaMemcpyDeviceToHost, s));
     JV_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> blk;
     h->maxrow = 0;
-    for (int r = 0; r < n;) {
-        blk.push_back(r);
-        int e = r + 1;
-        while (e < n && e - r < kSpmvRows && hrp[e + 1] - hrp[r] <= kSpmvCap) ++e;
-        for (int i = r; i < e; ++i) h->maxrow = std::max(h->maxrow, hrp[i + 1] - hrp[i]);
-        r = e;
+    for (int r = 0; r < n; ++r) h->maxrow = std::max(h->maxrow, hrp[r + 1] - hrp[r]);
+    {
+        std::vector<int> start((size_t)h->maxrow + 2, 0), srows((size_t)n);
+        for (int r = 0; r < n; ++r) ++start[h->maxrow - (hrp[r + 1] - hrp[r]) + 1];
+        for (int L = 0; L <= h->maxrow; ++L) start[L + 1] += start[L];
+        for (int r = 0; r < n; ++r) srows[start[h->maxrow - (hrp[r + 1] - hrp[r])]++] = r;
+        JV_TRY(halloc_n(h, &h->spmv_rows, n));
+        JV_CUDA(cudaMemcpyAsync(h->spmv_rows, srows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        JV_CUDA(cudaStreamSynchronize(s));
     }
-    blk.push_back(n);
-    h->nspmv_blk = (int)blk.size() - 1;
-    JV_TRY(halloc_n(h, &h->spmv_blk, blk.size()));
-    JV_CUDA(cudaMemcpyAsync(h->spmv_blk, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice, s));
 
     // binned work lists: the four solves and the factor
     int *dcost;
@@ -649,8 +661,20 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
         mid_rows += (c > kLaneSlot && c <= kLaneSlotWide);
     }
     h->fslot = 4 * mid_rows >= n ? kLaneSlotWide : kLaneSlot;
+    // rows above the one-lane slot that fit a group's share of the warp's
+    // shared memory (values and operands at 8 bytes, targets and step ends at
+    // 4), and whose L entries depend on each other (the pull form, for the
+    // others, spreads a row over the whole warp): kGroupLanes lanes each
+    std::vector<unsigned char> pull((size_t)n), grp((size_t)n, 0);
+    JV_CUDA(cudaMemcpyAsync(pull.data(), h->row_pull, (size_t)n, cudaMemcpyDeviceToHost, s));
+    JV_CUDA(cudaStreamSynchronize(s));
+    const long long gcap = (long long)factor_warp_smem(h->fslot) / (kWarp / kGroupLanes);
+    for (int i = 0; i < n; ++i) {
+        const long long c = cost[4 * (size_t)n + i], len = hrp[i + 1] - hrp[i];
+        grp[i] = (unsigned char)(!pull[i] && c * 8 + (c - len) * 4 <= gcap);
+    }
     JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, h->fslot, fops.data(),
-                     h->fbins));
+                     h->fbins, grp.data()));
     return plan_bands(h);
 }
 

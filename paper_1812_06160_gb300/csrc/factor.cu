@@ -375,13 +375,21 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     }
 }
 
-// ------------------------------------------------------- one warp per row
-template <class TV, class TL, bool SF, int S, bool RCP>
+// ----------------------------------------- G lanes per row (G = 8 or 32)
+// The row at work-list position pos, run by a group of G lanes: the whole
+// warp (a long task) or a quarter of it (a medium task of four rows: the
+// four groups run the same steps in lockstep when their rows have the same
+// shape, as the interior rows of a stencil do, so each FP64 warp instruction
+// serves four rows).  smem_bytes: the group's share of the warp's shared
+// memory; a row that does not fit works in the global scratch area.
+template <class TV, class TL, bool SF, bool RCP, int G>
 __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsigned gate,
-                                            unsigned char *smem) {
+                                            unsigned char *smem, int smem_bytes) {
     using B = Bits<TL>;
     using U = typename B::U;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned gmask = G == kWarp ? 0xffffffffu
+                                      : ((1u << G) - 1u) << ((threadIdx.x & (kWarp - 1)) & ~(G - 1));
     const int r = __ldg(a.rows + pos);
     const int rs = __ldg(a.rowptr + r), re = __ldg(a.rowptr + r + 1), rd = __ldg(a.diag + r);
     const int len = re - rs, nl = rd - rs;
@@ -393,22 +401,22 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     TL *piv = static_cast<TL *>(a.piv);
     const TV *vals = static_cast<const TV *>(a.vals);
     const size_t need = (size_t)(len + m) * sizeof(TL) + (size_t)(np + nl) * sizeof(int);
-    const bool fast = need <= (size_t)warp_smem<S>();
+    const bool fast = need <= (size_t)smem_bytes;
     TL *w = fast ? reinterpret_cast<TL *>(smem) : static_cast<TL *>(a.scratch) + rs;
     TL *uv = w + len;
     int *tgt = reinterpret_cast<int *>(uv + m);                // fast path only
     int *send = tgt + np;
-    for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
+    for (int e = lane; e < len; e += G) w[e] = (TL)__ldg(vals + rs + e);
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
     if (fast) {
-        for (int e = lane; e < np; e += kWarp) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
-        for (int e = lane; e < nl; e += kWarp) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
-        for (int e0 = 0; e0 < m; e0 += kWarp * kUnroll) {
+        for (int e = lane; e < np; e += G) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
+        for (int e = lane; e < nl; e += G) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
+        for (int e0 = 0; e0 < m; e0 += G * kUnroll) {
             int src[kUnroll];
             U u[kUnroll];
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k) {
-                const int e = e0 + k * kWarp + lane;
+                const int e = e0 + k * G + lane;
                 src[k] = -1;
                 if (e < m) {
                     if (e < nl) {                                  // the pivot of step e
@@ -428,13 +436,13 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k)
                 if (src[k] != -1) {
-                    const int e = e0 + k * kWarp + lane;
+                    const int e = e0 + k * G + lane;
                     if (SF && src[k] >= 0) u[k] = settle<TL>((e < nl ? piv : lu) + src[k], u[k], a, r, fail);
                     uv[e] = B::from(u[k]);
                 }
         }
     }
-    __syncwarp();
+    __syncwarp(gmask);
     int jb = 0;
     for (int p = 0; p < nl; ++p) {
         TL ukk;
@@ -448,7 +456,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         const int je = fast ? send[p] : __ldg(a.pair_ptr + rs + p + 1) - j0;
         // the targets of one step are distinct -- except, with MILU, the
         // diagonal, which lane 0 then updates alone, in the listed order
-        for (int j = jb + lane; j < je; j += kWarp) {
+        for (int j = jb + lane; j < je; j += G) {
             int t;
             TL uq;
             if (fast) {
@@ -478,23 +486,23 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
             }
         }
         jb = je;
-        __syncwarp();
+        __syncwarp(gmask);
         if (lane == 0) w[p] = lik;
     }
-    __syncwarp();
-    if (SF && __any_sync(0xffffffffu, fail)) return;
+    __syncwarp(gmask);
+    if (SF && __any_sync(gmask, fail)) return;
     if (lane == 0) pivot_check<TL>(a, r, w[nl]);
     if (lane == 0 && (!SF || r != a.fault_row)) {
         const TL pv = RCP ? rcp_newton(w[nl]) : w[nl];
         if (SF) publish<TL>(piv + pos, pv);
         else piv[pos] = pv;
     }
-    for (int e = lane; e < len; e += kWarp) {
+    for (int e = lane; e < len; e += G) {
         const TL v = w[e];
         if (!SF || e < nl) lu[rs + e] = v;
         else if (r != a.fault_row) publish<TL>(lu + rs + e, v);
     }
-    __syncwarp();                                              // shared memory reusable
+    __syncwarp(gmask);                                         // shared memory reusable
 }
 
 // ------------------------------------------- one warp per row, pull form
@@ -599,7 +607,12 @@ __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsig
         if (a.tpairs && __ldg(a.row_pull + __ldg(a.rows + lo)))
             factor_warp_pull<TV, TL, SF, S, RCP>(a, lo, gate, smem);
         else
-            factor_warp<TV, TL, SF, S, RCP>(a, lo, gate, smem);
+            factor_warp<TV, TL, SF, RCP, kWarp>(a, lo, gate, smem, warp_smem<S>());
+    } else if (hi & kGroupBit) {                 // kWarp / kGroupLanes rows, one per group
+        constexpr int share = warp_smem<S>() / (kWarp / kGroupLanes);
+        const int g = (threadIdx.x & (kWarp - 1)) / kGroupLanes;
+        if (lo + g < (hi & ~kGroupBit))
+            factor_warp<TV, TL, SF, RCP, kGroupLanes>(a, lo + g, gate, smem + g * share, share);
     }
     else factor_lanes<TV, TL, SF, W, S, RCP>(a, lo, hi, gate, smem);
     __syncwarp();
@@ -621,6 +634,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_ilu0(FactorArgs a) {
 }
 
 template <int S> constexpr int block_smem() { return kWarpsPerBlock * warp_smem<S>(); }
+
+}  // namespace
+
+int factor_warp_smem(int slot) {
+    return slot > kLaneSlot ? warp_smem<kLaneSlotWide>() : warp_smem<kLaneSlot>();
+}
+
+namespace {
 
 // Scratch: [0, nnz) work area for long rows, [nnz, 2 nnz) copy of the input
 // for in-place calls (8-byte elements, enough for either dtype).
@@ -674,7 +695,7 @@ int run(jv_handle h, const void *vals, void *lu) {
     const LevelSet &L = h->ls[JV_LOWER];
     cudaStream_t s = h->stream;
     const bool inplace = vals == lu;
-    if (inplace || W.nlong > 0) {
+    if (inplace || W.nlong > 0 || W.ngroup > 0) {
         int rc = ensure_scratch(h);
         if (rc) return rc;
     }

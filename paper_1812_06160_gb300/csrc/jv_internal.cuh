@@ -22,8 +22,6 @@ constexpr int kPoll = 8;          // largest poll window of the one-lane-per-row
 constexpr int kLongDeps = 24;     // solve rows with more dependencies run one per warp
 constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
 constexpr int kLaneSlotWide = 32; // the same, when many rows need 17..32 (e.g. MILU fill pairs)
-constexpr int kSpmvRows = 256;    // rows per spmv block (one summing thread each)
-constexpr int kSpmvCap = 2048;    // nonzeros per spmv block (8 per thread)
 
 // ---------------------------------------------------------------- launches
 extern std::atomic<unsigned long long> g_launches;
@@ -310,10 +308,14 @@ __device__ __forceinline__ int find_col(const int *__restrict__ col, int lo, int
 // Work list of one level structure, rows binned by cost (the row-length
 // classes of the load-balancing concern of Sec. III-A / III-B): inside every
 // level the short rows come first, in ascending order, packed 32 to a task
-// (16 where levels are narrow) with one lane per row; every long row is a
-// task of its own, run by the whole warp.  A task never spans two levels, so the rows of a task never
-// depend on each other.
+// (16 where levels are narrow) with one lane per row; in the factor's list,
+// medium rows follow, kWarp / kGroupLanes to a task with kGroupLanes lanes
+// per row (the sub-warp rows of a 27-point stencil); every long row is a
+// task of its own, run by the whole warp.  A task never spans two levels, so
+// the rows of a task never depend on each other.
 constexpr int kLongBit = (int)0x80000000u;   // task_hi flag: one-row cooperative task
+constexpr int kGroupBit = 0x40000000;        // task_hi flag (factor): rows of kGroupLanes lanes each
+constexpr int kGroupLanes = 8;
 struct Bins {
     int *rows = nullptr;       // [n] binned rows
     int *ipos = nullptr;       // [n] position of every row in rows (inverse of rows)
@@ -323,6 +325,7 @@ struct Bins {
     int *task_ptr = nullptr;   // [nlev+1] first task of every level (device copy)
     int ntasks = 0;
     int nlong = 0;
+    int ngroup = 0;            // factor: tasks of kWarp / kGroupLanes rows, kGroupLanes lanes each
     int window = 8;            // operands a one-lane row polls per round: 2, 4, 8 or 16,
                                // the smallest holding the most operands of any short
                                // row; 17 = more (rows span several windows of kPoll)
@@ -452,9 +455,7 @@ struct jv_handle_s {
     jv::CornerPlan corner[2];                // Even-Rows corner per factor dtype (jv_dtype)
     jv::SolveCorner scorner[4][2];           // per structure; [1]: lu and x both FP32
     int maxrow = 0;                          // longest row
-    // spmv row blocks: block b covers rows [spmv_blk[b], spmv_blk[b+1])
-    int *spmv_blk = nullptr;
-    int nspmv_blk = 0;
+    int *spmv_rows = nullptr;                // spmv: rows by length, longest first
     // lazily allocated factor scratch (long rows / in-place copies)
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;
@@ -528,6 +529,8 @@ int keys_to_ptr(const unsigned *sorted_keys, int m, int *ptr, int K, cudaStream_
 int analyze(jv_handle h, const int *rowptr, const int *colidx);
 
 // factor.cu
+// shared memory of one factor warp for a one-lane slot of `slot` words
+int factor_warp_smem(int slot);
 int ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals, jv_dtype lu_t, void *lu);
 
 // band.cu: band schedule planner (host) and the band kernels

@@ -19,64 +19,64 @@ template <> struct RN<float> {
     __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
 };
 
-// One CTA per row block (at most kSpmvRows rows and kSpmvCap nonzeros, fixed
-// by the analysis): the block's nonzeros are streamed with fully coalesced
-// loads, each thread keeping several independent loads in flight, and staged
-// in shared memory together with the gathered x_j; then one thread per row
-// accumulates s = fma(a_ij, x_j, s) in ascending column order -- the serial
-// spmv's sequence, so the result is identical to it.  A row longer than the
-// cap has a block of its own and is walked in chunks.
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_spmv(const int *__restrict__ blk,
-                                                 const int *__restrict__ rowptr,
-                                                 const int *__restrict__ colidx,
-                                                 const T *__restrict__ vals,
-                                                 const T *__restrict__ x, T *y, T alpha, T beta,
-                                                 int has_beta) {
-    __shared__ T sv[kSpmvCap];
-    __shared__ T sx[kSpmvCap];
-    const int r0 = __ldg(blk + blockIdx.x), r1 = __ldg(blk + blockIdx.x + 1);
-    const int p0 = __ldg(rowptr + r0), p1 = __ldg(rowptr + r1);
-    const int tid = threadIdx.x;
-    if (p1 - p0 <= kSpmvCap) {
-        const int m = p1 - p0;
-#pragma unroll 8
-        for (int e = tid; e < m; e += kBlock) {
-            const int q = p0 + e;
-            sv[e] = __ldg(vals + q);
-            sx[e] = __ldg(x + __ldg(colidx + q));
-        }
-        __syncthreads();
-        for (int i = tid; i < r1 - r0; i += kBlock) {
-            const int r = r0 + i;
-            const int e1 = __ldg(rowptr + r + 1) - p0;
-            T s = 0;
-            for (int e = __ldg(rowptr + r) - p0; e < e1; ++e) s = RN<T>::fma(sv[e], sx[e], s);
-            T v = RN<T>::mul(alpha, s);
-            if (has_beta) v = RN<T>::fma(beta, y[r], v);
-            y[r] = v;
-        }
-    } else {
-        T s = 0;
-        for (int c0 = p0; c0 < p1; c0 += kSpmvCap) {
-            const int m = min(kSpmvCap, p1 - c0);
-#pragma unroll 8
-            for (int e = tid; e < m; e += kBlock) {
-                const int q = c0 + e;
-                sv[e] = __ldg(vals + q);
-                sx[e] = __ldg(x + __ldg(colidx + q));
-            }
-            __syncthreads();
-            if (tid == 0)
-                for (int e = 0; e < m; ++e) s = RN<T>::fma(sv[e], sx[e], s);
-            __syncthreads();
-        }
-        if (tid == 0) {
-            T v = RN<T>::mul(alpha, s);
-            if (has_beta) v = RN<T>::fma(beta, y[r0], v);
-            y[r0] = v;
+// One lane per row, in the serial order of every row (each product added
+// with one fused multiply-add in ascending column order -- the serial spmv's
+// sequence, so the result is identical to it).  A warp instruction of the
+// FP64 pipe costs 64 cycles on this part whatever its active lanes, and a
+// row's chain of fused multiply-adds cannot be split without changing the
+// result, so the rows are taken in order of length, longest first (the
+// analysis sorts them once): the 32 rows of a warp have about the same
+// length, every FP64 instruction works on 32 rows, and the longest chains
+// start first.  A lane streams its row in chunks of U entries through a
+// three-stage pipeline -- indices and values of chunk c+2 loading, x of chunk
+// c+1 being gathered, chunk c being summed -- so a long row's loads stay
+// ahead of its chain.
+template <class T, int U>
+__global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict__ srows,
+                                                    const int *__restrict__ rowptr,
+                                                    const int *__restrict__ colidx,
+                                                    const T *__restrict__ vals,
+                                                    const T *__restrict__ x, T *y, T alpha, T beta,
+                                                    int has_alpha, int has_beta) {
+    const long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+    if (t >= n) return;
+    const int r = __ldg(srows + t);
+    const int p0 = __ldg(rowptr + r), p1 = __ldg(rowptr + r + 1);
+    int j2[U];
+    T a1[U], x1[U], a2[U];
+    // chunk 0: indices and values, then its gathers; chunk 1: indices and values
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+        if (p0 + k < p1) { j2[k] = __ldg(colidx + p0 + k); a1[k] = __ldg(vals + p0 + k); }
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+        if (p0 + k < p1) x1[k] = __ldg(x + j2[k]);
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+        if (p0 + U + k < p1) { j2[k] = __ldg(colidx + p0 + U + k); a2[k] = __ldg(vals + p0 + U + k); }
+    T s = 0;
+    for (int c = p0; c < p1; c += U) {
+        T x2[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k)                       // gathers of chunk c+1
+            if (c + U + k < p1) x2[k] = __ldg(x + j2[k]);
+        T a3[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k)                       // indices and values of chunk c+2
+            if (c + 2 * U + k < p1) { j2[k] = __ldg(colidx + c + 2 * U + k); a3[k] = __ldg(vals + c + 2 * U + k); }
+#pragma unroll
+        for (int k = 0; k < U; ++k)                       // the chain of chunk c
+            if (c + k < p1) s = RN<T>::fma(a1[k], x1[k], s);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            a1[k] = a2[k];
+            x1[k] = x2[k];
+            a2[k] = a3[k];
         }
     }
+    T v = has_alpha ? RN<T>::mul(alpha, s) : s;            // alpha = 1: the product is s exactly
+    if (has_beta) v = RN<T>::fma(beta, y[r], v);
+    y[r] = v;
 }
 
 // 16-byte vector of T: four floats or two doubles
@@ -146,17 +146,17 @@ __global__ void k_permute_rows(int n, int nrhs, const int *perm, int inverse, co
 
 int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, double alpha,
          double beta) {
-    const int grid = h->nspmv_blk;
-    const int hb = beta != 0.0;
+    const int grid = grid_for(h->n, kBlock);
+    const int hb = beta != 0.0, ha = alpha != 1.0;
     count_launch();
     if (t == JV_F64)
-        k_spmv<double><<<grid, kBlock, 0, h->stream>>>(h->spmv_blk, h->rowptr, h->colidx,
-                                                       (const double *)vals, (const double *)x,
-                                                       (double *)y, alpha, beta, hb);
+        k_spmv<double, 4><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
+                                                          (const double *)vals, (const double *)x,
+                                                          (double *)y, alpha, beta, ha, hb);
     else if (t == JV_F32)
-        k_spmv<float><<<grid, kBlock, 0, h->stream>>>(h->spmv_blk, h->rowptr, h->colidx,
-                                                      (const float *)vals, (const float *)x,
-                                                      (float *)y, (float)alpha, (float)beta, hb);
+        k_spmv<float, 8><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
+                                                         (const float *)vals, (const float *)x,
+                                                         (float *)y, (float)alpha, (float)beta, ha, hb);
     else
         return JV_ERR_ARG;
     JV_CHECK_LAUNCH();
