@@ -152,22 +152,27 @@ typedef struct {
                                        buffers and mode replay it (up to 16 graphs per
                                        handle; inside a stream capture of the caller's own
                                        the launches go into that capture). */
-    int exact_division;             /* 1: the FP64 factor and the FP64 U / U^T solves divide
-                                       by each pivot as Fig. 1 and back substitution do,
-                                       every operation in the serial algorithm's order, so
-                                       FP64 results equal the serial algorithm's bit for
-                                       bit.  0 (default): the FP64 factor's row k computes
-                                       1/u_kk once, by Newton's iteration, when u_kk is
-                                       final and publishes it beside the factor; every
-                                       multiplier is then l_ik = a_ik * (1/u_kk), within a
-                                       few units in the last place of the quotient (the
-                                       division sequence it replaces is the longest run of
-                                       FP64 work on the critical path).  The U / U^T solves
-                                       form s / u_ii from 1/u_ii, computed before a row's
-                                       operands arrive, with one correction step
-                                       (Markstein's), which gives the division's result
-                                       with fewer instructions after the last operand.
-                                       FP32 always divides (its pipe is full width). */
+    int exact;                      /* 1: every FP64 result equals the serial algorithm's
+                                       bit for bit: the factor divides by each pivot as
+                                       Fig. 1 does, and every sum runs in the serial order.
+                                       0 (default), two departures, each within a few
+                                       units in the last place per operation:
+                                       - the FP64 factor's row k computes 1/u_kk once, by
+                                         Newton's iteration, when u_kk is final, and every
+                                         multiplier is l_ik = a_ik * (1/u_kk) (the
+                                         division sequence it replaces is the longest run
+                                         of FP64 work on the critical path);
+                                       - a solve row with more dependencies than long_row
+                                         splits its sum over the warp's lanes (each lane's
+                                         share in ascending order, then a fixed tree), so
+                                         its chain is about 1/32 as long; the result is
+                                         deterministic run to run.
+                                       Either way the U / U^T solves form s / u_ii from
+                                       1/u_ii, computed before a row's operands arrive,
+                                       and one correction step (Markstein's), which gives
+                                       the division's own result, the one-lane solve rows
+                                       and the factor's other arithmetic keep the serial
+                                       order, and FP32 divides (its pipe is full width). */
 } jv_options;
 
 typedef struct {

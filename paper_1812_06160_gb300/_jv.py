@@ -44,7 +44,7 @@ class jv_options(ctypes.Structure):
                 ("milu", ctypes.c_int), ("sym_levels", ctypes.c_int),
                 ("stage_min_rows", ctypes.c_int), ("stage_max_density", ctypes.c_double),
                 ("stage_position", ctypes.c_double), ("er_corner", ctypes.c_int),
-                ("no_graphs", ctypes.c_int), ("exact_division", ctypes.c_int)]
+                ("no_graphs", ctypes.c_int), ("exact", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
@@ -201,7 +201,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
                spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0,
                band_rows=0, sf_gate_levels=None, milu=False, sym_levels=False,
                stage_min_rows=0, stage_max_density=0.0, stage_position=0.0, er_corner=False,
-               graphs=True, exact_division=False):
+               graphs=True, exact=False):
     """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle.
     ``mode``: "level", "syncfree" or "hybrid" (the two-stage split of Sec. III-A,
     with the stage test ``stage_min_rows`` / ``stage_max_density`` /
@@ -232,7 +232,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
     opt.stage_position = float(stage_position)
     opt.er_corner = int(bool(er_corner))
     opt.no_graphs = int(not graphs)
-    opt.exact_division = int(bool(exact_division))
+    opt.exact = int(bool(exact))
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):

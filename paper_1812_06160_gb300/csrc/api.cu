@@ -101,7 +101,7 @@ void jv_default_options(jv_options *opt) {
     opt->stage_position = 0.0;
     opt->er_corner = 0;
     opt->no_graphs = 0;
-    opt->exact_division = 0;
+    opt->exact = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {

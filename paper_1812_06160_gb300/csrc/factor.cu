@@ -37,7 +37,7 @@
 // updated u_kq are polled (for a 5- or 7-point stencil, only the pivots, and
 // lu then needs no sentinel fill).
 //
-// Reciprocal pivots (RCP, FP64 unless jv_options.exact_division): the pivot
+// Reciprocal pivots (RCP, FP64 unless jv_options.exact): the pivot
 // a row publishes is y_k = 1/u_kk (Newton's iteration, rcp_newton), and a
 // dependant forms l_rk = a_rk * y_k.  On this part a warp instruction of the FP64 pipe costs
 // 64 cycles whatever its active lanes, and the three correctly rounded
@@ -543,11 +543,34 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
     TL *piv = static_cast<TL *>(a.piv);
-    for (int e = lane; e < nl; e += kWarp) {               // u_kk, or its reciprocal (RCP)
-        const TL *src = piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
-        ukk[e] = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
+    // the operands, kUnroll per lane at a time: the loads of a batch are issued
+    // together, then each is awaited (most are final long before: a long row
+    // reads rows of many earlier levels)
+    for (int e0 = 0; e0 < nl + nq; e0 += kWarp * kUnroll) {
+        const TL *src[kUnroll];
+        typename B::U u[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            const int e = e0 + k * kWarp + lane;
+            src[k] = nullptr;
+            if (e < nl) {                                  // u_kk, or its reciprocal (RCP)
+                src[k] = piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
+            } else if (e < nl + nq) {                      // u_kq
+                const int q = __ldg(a.tpairs + s0 + e - nl).y;
+                if (__ldg(a.upd + q)) src[k] = static_cast<const TL *>(a.lu) + q;
+                else u[k] = B::to((TL)__ldg(vals + q));   // final from the start
+            }
+            if (src[k]) u[k] = first_read<TL, SF>(src[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            const int e = e0 + k * kWarp + lane;
+            if (e >= nl + nq) continue;
+            if (SF && src[k]) u[k] = settle<TL>(src[k], u[k], a, r, fail);
+            if (e < nl) ukk[e] = B::from(u[k]);
+            else uq[e - nl] = B::from(u[k]);
+        }
     }
-    for (int e = lane; e < nq; e += kWarp) uq[e] = pair_operand<TV, TL, SF>(a, __ldg(a.tpairs + s0 + e).y, r, fail);
     __syncwarp();
     // L entries: chunks of 32, waves inside a chunk
     for (int c0 = 0; c0 < nl; c0 += kWarp) {
@@ -717,7 +740,7 @@ int run(jv_handle h, const void *vals, void *lu) {
         }
     }
     // reciprocal pivots: FP64 factors unless exact division is asked for
-    const bool rcp = sizeof(TL) == 8 && !h->opt.exact_division;
+    const bool rcp = sizeof(TL) == 8 && !h->opt.exact;
     if (h->piv_bytes < (size_t)h->n * sizeof(TL)) {          // the pivot array
         if (h->piv) {
             JV_CUDA(cudaStreamSynchronize(s));

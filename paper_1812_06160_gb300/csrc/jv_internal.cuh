@@ -245,7 +245,7 @@ template <> struct Bits<float> {
     }
 };
 
-// 1/d for the FP64 factor and back substitution (jv_options.exact_division =
+// 1/d for the FP64 factor and back substitution (jv_options.exact =
 // 0): Newton's iteration for the reciprocal, y <- y + y (1 - d y), which
 // squares the relative error at every step, started from the approximate
 // reciprocal the hardware provides (PTX rcp.approx.ftz.f64).  Two steps take

@@ -12,7 +12,7 @@
 // loads run in parallel.  (FP64 U and U^T solves form s / u_rr from 1/u_rr,
 // computed while the row waits, and one correction -- the same quotient as
 // the division, with a third of its instructions after the last operand
-// arrives -- unless jv_options.exact_division asks for the division itself.)
+// arrives -- unless jv_options.exact asks for the division itself.)
 //
 // Work list (see Bins): a short task holds up to 32 rows of one level, one
 // lane per row.  Every lane polls the next W dependencies of its own row (a
@@ -22,7 +22,11 @@
 // consumes the ready prefix in order and publishes its row the moment the
 // last one arrives, so no lane waits for another lane's dependencies.  A
 // long task is one row with many dependencies; the whole warp loads 32 x
-// kUnroll of them at a time and replays the ordered chain through shuffles.
+// kUnroll of them at a time and replays the ordered chain through shuffles
+// (jv_options.exact), or, by default, every lane sums its own share in
+// ascending order and a fixed tree combines the 32 shares: a chain about a
+// 32nd as long (a 2,000-entry row of the power-law matrix was a chain of
+// 2,000 dependent FP64 operations), deterministic, but not the serial order.
 // Several right-hand sides: one warp per row, one lane per right-hand side
 // (row-major n x nrhs: the lanes read one contiguous segment of every
 // dependency row).
@@ -46,6 +50,8 @@ struct TriArgs {
     int unit;              // 1: unit diagonal (L, L^T)
     int rcp;               // FP64 U, U^T: divide through 1/u_rr (rcp_newton, computed before
                            // the row's operands arrive) and one correction (div_rcp)
+    int tree;              // long rows: lanes sum their shares, then a fixed tree (not the
+                           // serial order; jv_options.exact = 0)
     int reverse;           // 1: walk the range from its end (L^T)
     const int *rows, *task_lo, *task_hi;
     int task_begin, task_end;
@@ -365,6 +371,7 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
     TL dy = 1;
     const TL d = a.unit ? (TL)1 : load_diag<TL>(a, r, dy);
     bool fail = false;                 // a wait gave up: publish nothing
+    TL part = 0;                       // tree: this lane's share of the sum
     for (int c0 = 0; c0 < len; c0 += CH) {
         int q[kUnroll];
         TL v[kUnroll];
@@ -390,14 +397,25 @@ __device__ __forceinline__ void trsv_warp(const TriArgs &a, int pos) {
                 v[k] = 0;
             }
         }
-        // the ordered chain: entry c0 + k*32 + l is held by lane l
+        if (a.tree) {
+            // each lane's share, in ascending order (absent entries are 0 * 0)
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k)
-            for (int l = 0; l < kWarp; ++l) {
-                const TL vl = __shfl_sync(0xffffffffu, v[k], l);
-                const TL xl = __shfl_sync(0xffffffffu, xv[k], l);
-                if (c0 + k * kWarp + l < len) s = RN<TL>::fms(vl, xl, s);
-            }
+            for (int k = 0; k < kUnroll; ++k) part = RN<TL>::fms(v[k], xv[k], part);
+        } else {
+            // the ordered chain: entry c0 + k*32 + l is held by lane l
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k)
+                for (int l = 0; l < kWarp; ++l) {
+                    const TL vl = __shfl_sync(0xffffffffu, v[k], l);
+                    const TL xl = __shfl_sync(0xffffffffu, xv[k], l);
+                    if (c0 + k * kWarp + l < len) s = RN<TL>::fms(vl, xl, s);
+                }
+        }
+    }
+    if (a.tree) {                      // the lanes' shares combined by a fixed tree
+#pragma unroll
+        for (int off = kWarp / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        s += part;
     }
     if (SF && __any_sync(0xffffffffu, fail)) return;
     if (lane == 0) store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
@@ -539,7 +557,8 @@ int run(jv_handle h, int structure, const void *lu, const void *b, void *x, int 
     a.timeout = h->opt.spin_timeout_cycles > 0 ? h->opt.spin_timeout_cycles : kDefaultSpin;
     a.fault_row = h->opt.fault_row;
     a.backoff_ns = sf_backoff(h);
-    a.rcp = sizeof(TL) == 8 && !h->opt.exact_division;
+    a.rcp = sizeof(TL) == 8 && !h->opt.exact;
+    a.tree = !h->opt.exact;
     // a one-column solve may end in an Even-Rows corner: the upper stage
     // then runs the levels above it
     const SolveCorner *C = multi ? nullptr : solve_corner_of(h, structure, sizeof(TL), sizeof(TX));

@@ -12,11 +12,11 @@ def analyze(jv, rowptr, colidx, schedule, **kw):
     (one persistent launch over level-ordered tasks), 'band' (sync-free band
     schedule, forced with a small band so it meets every pattern).  The
     handle divides by every pivot as the serial algorithm does
-    (exact_division) unless the caller asks otherwise: the bit-exact tests
+    (exact) unless the caller asks otherwise: the bit-exact tests
     compare that mode with the oracle, the tests of the default mode pass
-    exact_division=False and compare within tolerance."""
+    exact=False and compare within tolerance."""
     import torch
-    kw.setdefault("exact_division", True)
+    kw.setdefault("exact", True)
     rp = torch.tensor(np.asarray(rowptr), device="cuda")
     ci = torch.tensor(np.asarray(colidx), device="cuda")
     if schedule == "level":

@@ -43,9 +43,9 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False, exact=False
     (row-scaled floor of jvutil.close), the raw largest error printed, and
     the solves bit-exact with the oracle's solves on the same factor."""
     if mode == "auto":        # the benchmark's configuration: sync-free, schedule chosen by the analysis
-        h = jv.jv_analyze(T(rp), T(ci), reorder=reorder, exact_division=exact)
+        h = jv.jv_analyze(T(rp), T(ci), reorder=reorder, exact=exact)
     else:
-        h = analyze(jv, rp, ci, mode, reorder=reorder, exact_division=exact)
+        h = analyze(jv, rp, ci, mode, reorder=reorder, exact=exact)
     if reorder:
         _, _, _, perm = O.level_sets(rp, ci)
         _, rp, ci, vmap = O.permute(rp, ci, perm)
@@ -78,12 +78,20 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False, exact=False
             assert np.array_equal(y.cpu().numpy(), oy)
             assert np.array_equal(z.cpu().numpy(), oz)
         else:
-            # each kernel against the oracle on the same inputs: the solves
-            # on the GPU's factor are the serial ones bit for bit
+            # each kernel against the oracle on the same inputs: the solves on
+            # the GPU's factor are the serial ones bit for bit, or, where rows
+            # above long_row sum by lanes and a tree, within 1e-12
             glu = lu.cpu().numpy()
+            nlong = jv.jv_get_info(h)["nlong"]
             gy = O.lsolve(rp, ci, diag, glu, bb)
-            assert np.array_equal(y.cpu().numpy(), gy)
-            assert np.array_equal(z.cpu().numpy(), O.usolve(rp, ci, diag, glu, gy))
+            gz = O.usolve(rp, ci, diag, glu, y.cpu().numpy())
+            for k, (name, got, want) in enumerate((("lsolve", y, gy), ("usolve", z, gz))):
+                if nlong[k] == 0:
+                    assert np.array_equal(got.cpu().numpy(), want), name
+                else:
+                    ok, err = close(got.cpu().numpy(), want)
+                    print(f"{name} on the GPU factor: largest relative error {err:.2e}")
+                    assert ok, (name, err)
             # the whole pipeline against the oracle's (its own factor) is
             # reported, not bounded: the triangular recurrences amplify the
             # factor's last-place differences by the conditioning of L and U
@@ -105,7 +113,7 @@ def test_c2_lap7_128_fp64(mode):
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], mode)
 
 
-def test_c2_lap7_128_fp64_exact_division():
+def test_c2_lap7_128_fp64_exact():
     c = cfg("c2")
     _full_check(c["rowptr"], c["colidx"], c["vals"], c["b"], "auto", exact=True)
 
@@ -131,7 +139,7 @@ def test_c5_aniso_1024_32rhs():
     rp, ci, v, B, g = c["rowptr"], c["colidx"], c["vals"], c["b"], c["g"]
     diag = O.diag_ptr(rp, ci)
     olu32, _, _ = O.ilu0(rp, ci, v.astype(np.float32), diag, dtype=np.float32)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True)
     lu = jv.jv_ilu0_factor(h, T(v), lu_dtype=torch.float32)
     assert np.array_equal(lu.cpu().numpy(), olu32)
     lu64 = olu32.astype(np.float64)

@@ -25,7 +25,7 @@ def test_replay_bit_exact_and_reads_current_buffers(mode):
     diag = O.diag_ptr(rp, ci)
     olu, st, _ = O.ilu0(rp, ci, v)
     assert st == O.OK
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode=mode, stage_min_rows=20)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, mode=mode, stage_min_rows=20)
     vals = T(v)
     lu = torch.empty_like(vals)
     counts = []
@@ -57,8 +57,8 @@ def test_replay_bit_exact_and_reads_current_buffers(mode):
 
 def test_graphs_off_matches():
     rp, ci, v = W.aniso5(40)
-    h1 = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode="level")
-    h0 = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode="level", graphs=False)
+    h1 = jv.jv_analyze(T(rp), T(ci), exact=True, mode="level")
+    h0 = jv.jv_analyze(T(rp), T(ci), exact=True, mode="level", graphs=False)
     vals = T(v)
     for _ in range(2):
         lu1 = jv.jv_ilu0_factor(h1, vals)
@@ -73,7 +73,7 @@ def test_caller_capture_takes_the_launches():
     n = len(rp) - 1
     diag = O.diag_ptr(rp, ci)
     olu, _, _ = O.ilu0(rp, ci, v)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode="level", check=False)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, mode="level", check=False)
     lu = T(olu)
     b = T(W.rhs(n, 1, seed=1))
     y = torch.empty_like(b)

@@ -41,7 +41,7 @@ def test_iluk_pattern_bit_exact(case, level):
     assert np.array_equal(fv.cpu().numpy(), want)
     # numeric ILU(k): the ILU(0) sweep on the filled pattern
     olu, st, bad = O.ilu0(frp, fci, want)
-    h = jv.jv_analyze(grp, gci, exact_division=True)
+    h = jv.jv_analyze(grp, gci, exact=True)
     if st != O.OK:
         with pytest.raises(jv.JvError) as e:
             jv.jv_ilu0_factor(h, fv)
@@ -72,7 +72,7 @@ def test_iluk_full_size(cfg, level):
     fv = jv.jv_scatter_values(T(rp), T(ci), T(v), grp, gci)
     olu, st, _ = O.ilu0(frp, fci, O.scatter_values(rp, ci, v, frp, fci))
     assert st == O.OK
-    h = jv.jv_analyze(grp, gci, exact_division=True)
+    h = jv.jv_analyze(grp, gci, exact=True)
     lu = jv.jv_ilu0_factor(h, fv)
     assert np.array_equal(lu.cpu().numpy(), olu)
     if cfg == "c2":
@@ -80,7 +80,7 @@ def test_iluk_full_size(cfg, level):
         # zeros on the fill) needs fewer iterations than with ILU(0)
         b = T(c["b"])
         _, info = jv.jv_pcg(h, fv, lu, b, tol=1e-8)
-        h0 = jv.jv_analyze(T(rp), T(ci), exact_division=True)
+        h0 = jv.jv_analyze(T(rp), T(ci), exact=True)
         vt = T(v)
         _, info0 = jv.jv_pcg(h0, vt, jv.jv_ilu0_factor(h0, vt), b, tol=1e-8)
         assert info["converged"] and info["iters"] < info0["iters"]

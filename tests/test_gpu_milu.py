@@ -42,7 +42,7 @@ def test_milu_factor_bit_exact(case, mode):
 def test_milu_band_schedule_rejected():
     rp, ci, v = W.lap5(8)
     with pytest.raises(jv.JvError) as e:
-        jv.jv_analyze(T(rp), T(ci), exact_division=True, milu=True, band_rows=64)
+        jv.jv_analyze(T(rp), T(ci), exact=True, milu=True, band_rows=64)
     assert e.value.status == jv.JV_ERR_ARG
 
 
@@ -52,7 +52,7 @@ def test_milu_full_size_bit_exact_and_row_sums(cfg):
     rp, ci, v = c["rowptr"], c["colidx"], c["vals"]
     olu, st, _ = O.ilu0(rp, ci, v, milu=True)
     assert st == O.OK
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, milu=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, milu=True)
     lu = jv.jv_ilu0_factor(h, T(v))
     assert np.array_equal(lu.cpu().numpy(), olu)
     # row sums: L U e == A e (to rounding), through the library's own solves:
@@ -63,7 +63,7 @@ def test_milu_full_size_bit_exact_and_row_sums(cfg):
     z = jv.jv_usolve(h, lu, jv.jv_lsolve(h, lu, ae))
     assert (z - e).abs().max().item() <= 1e-9
     # plain ILU(0) does not keep them (there is dropped fill on these patterns)
-    h0 = jv.jv_analyze(T(rp), T(ci), exact_division=True)
+    h0 = jv.jv_analyze(T(rp), T(ci), exact=True)
     lu0 = jv.jv_ilu0_factor(h0, T(v))
     z0 = jv.jv_usolve(h0, lu0, jv.jv_lsolve(h0, lu0, ae))
     assert (z0 - e).abs().max().item() > 1e-6

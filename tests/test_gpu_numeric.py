@@ -42,7 +42,7 @@ def test_factor_fp64_reciprocal_pivots_within_1e12(case, mode):
     # the default FP64 factor multiplies by each pivot's reciprocal: every
     # entry within 1e-12 relative of the oracle's divisions
     _, rp, ci, v = case
-    h = analyze(jv, rp, ci, mode, exact_division=False)
+    h = analyze(jv, rp, ci, mode, exact=False)
     lu = jv.jv_ilu0_factor(h, T(v)).cpu().numpy()
     olu, st, _ = O.ilu0(rp, ci, v)
     assert st == 0
@@ -53,22 +53,28 @@ def test_factor_fp64_reciprocal_pivots_within_1e12(case, mode):
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("nrhs", [1, 3, 33])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_solves_fp64_reciprocal_diagonal(case, nrhs, mode):
+def test_solves_fp64_default_mode(case, nrhs, mode):
     # default mode: the U and U^T solves form s / u_ii from 1/u_ii and one
-    # correction step, which gives the division's own result: all four
-    # solves stay bit-exact
+    # correction step, which gives the division's own result, so a structure
+    # of short rows solves bit-exactly; a structure with rows above long_row
+    # sums those rows by lanes and a fixed tree (one column): within 1e-12
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = analyze(jv, rp, ci, mode, exact_division=False)
+    h = analyze(jv, rp, ci, mode, exact=False)
+    nlong = jv.jv_get_info(h)["nlong"]
     olu, _, _ = O.ilu0(rp, ci, v)
     diag = O.diag_ptr(rp, ci)
     b = W.rhs(n, nrhs, seed=17 + nrhs)
     lu, bt = T(olu), T(b)
-    for name, ofn in (("jv_lsolve", O.lsolve), ("jv_usolve", O.usolve),
-                      ("jv_lsolve_t", O.lsolve_t), ("jv_usolve_t", O.usolve_t)):
+    for k, (name, ofn) in enumerate((("jv_lsolve", O.lsolve), ("jv_usolve", O.usolve),
+                                     ("jv_usolve_t", O.usolve_t), ("jv_lsolve_t", O.lsolve_t))):
         x = getattr(jv, name)(h, lu, bt).cpu().numpy()
         want = ofn(rp, ci, diag, olu, b)
-        assert np.array_equal(x, want), (name, close(x, want)[1])
+        if nlong[k] == 0 or nrhs > 1 or mode == "band":
+            assert np.array_equal(x, want), (name, close(x, want)[1])
+        else:
+            ok, err = close(x, want)
+            assert ok, (name, err)
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -134,7 +140,7 @@ def test_solves_fp32_and_mixed(case, mode):
 def test_spmv(case):
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True)
     x = W.rhs(n, 1, seed=3)
     y0 = W.rhs(n, 1, seed=4)
     scale = O.spmv(rp, ci, np.abs(v), np.abs(x)) + np.abs(y0)
@@ -157,7 +163,7 @@ def test_masked_outer(case, nrhs):
     # ones (powerlaw6000) the warp-per-row kernel
     _, rp, ci, _ = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True)
     diag = O.diag_ptr(rp, ci)
     a, b = W.rhs(n, nrhs, seed=1), W.rhs(n, nrhs, seed=2)
     for which in (0, 1):
@@ -186,7 +192,7 @@ def test_reordered_factor_and_solve(case):
     up to summation order)."""
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True)
     _, _, _, perm = O.level_sets(rp, ci)
     iperm, brp, bci, vmap = O.permute(rp, ci, perm)
     vb = jv.jv_permute_values(h, T(v))

@@ -65,7 +65,7 @@ def test_hybrid_launch_plan_follows_stage_test(case):
     deps = dep_counts(rp, ci)
     for min_rows, dens, pos in [(1, 0, 0), (10 ** 9, 0, 0), (16, 0, 0), (8, 1.5, 0),
                                 (4, 0, 0.5), (2, 1.0, 0.7)]:
-        h = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode="hybrid", stage_min_rows=min_rows,
+        h = jv.jv_analyze(T(rp), T(ci), exact=True, mode="hybrid", stage_min_rows=min_rows,
                           stage_max_density=dens, stage_position=pos)
         info = jv.jv_get_info(h)
         for k, which in enumerate(("L", "U", "Ut", "Lt")):
@@ -83,7 +83,7 @@ def test_hybrid_launch_plan_follows_stage_test(case):
 def test_hybrid_bit_exact(case, min_rows):
     _, rp, ci, v = case
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode="hybrid", stage_min_rows=min_rows)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, mode="hybrid", stage_min_rows=min_rows)
     olu, st, bad = O.ilu0(rp, ci, v)
     if st != O.OK:
         with pytest.raises(jv.JvError) as e:
@@ -134,7 +134,7 @@ def check_corner_info(h, brp, bci, min_rows):
 def test_er_corner_bit_exact(case, min_rows, mode):
     _, rp, ci, v = case
     brp, bci, bv = reordered(rp, ci, v)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, er_corner=True, mode=mode,
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, er_corner=True, mode=mode,
                       stage_min_rows=min_rows)
     info = check_corner_info(h, brp, bci, min_rows or 1024)
     assert info["corner_rows"][1] >= info["corner_rows"][0]
@@ -164,7 +164,7 @@ def test_er_corner_bit_exact(case, min_rows, mode):
 def test_er_corner_milu_bit_exact(case):
     _, rp, ci, v = case
     brp, bci, bv = reordered(rp, ci, v)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, er_corner=True, milu=True, stage_min_rows=6)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, er_corner=True, milu=True, stage_min_rows=6)
     olu, st, bad = O.ilu0(brp, bci, bv, milu=True)
     vb = jv.jv_permute_values(h, T(v))
     if st != O.OK:
@@ -182,7 +182,7 @@ def test_er_corner_zero_pivot_inside_corner():
     rp, ci, v = W.lap5(12)
     brp, bci, bv = reordered(rp, ci, v)
     n = len(brp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, er_corner=True, stage_min_rows=6)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, er_corner=True, stage_min_rows=6)
     R = jv.jv_get_info(h)["corner_rows"][0]
     assert 1 < R < n
     r0 = n - R
@@ -202,19 +202,19 @@ def test_er_corner_needs_trailing_rows():
     # 63} -- not the last six rows
     rp, ci, v = W.lap5(8)
     with pytest.raises(jv.JvError) as e:
-        jv.jv_analyze(T(rp), T(ci), exact_division=True, er_corner=True, stage_min_rows=4)
+        jv.jv_analyze(T(rp), T(ci), exact=True, er_corner=True, stage_min_rows=4)
     assert e.value.status == jv.JV_ERR_ARG
     # a corner that is the whole matrix fits any order (no row above it)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, er_corner=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, er_corner=True)
     assert jv.jv_get_info(h)["corner_rows"] == [64, 64]
     olu, _, _ = O.ilu0(rp, ci, v)
     assert np.array_equal(jv.jv_ilu0_factor(h, T(v)).cpu().numpy(), olu)
     with pytest.raises(jv.JvError) as e:
-        jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, er_corner=True, band_rows=64)
+        jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, er_corner=True, band_rows=64)
     assert e.value.status == jv.JV_ERR_ARG
     # a tridiagonal matrix is level-ordered as it stands: no reordering needed
     rp, ci, v = W.stencil((50, 1, 1), [(-1, 0, 0), (1, 0, 0)], [-1.0, -1.0], 4.0)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, er_corner=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, er_corner=True)
     assert jv.jv_get_info(h)["corner_rows"][0] == 50
     olu, _, _ = O.ilu0(rp, ci, v)
     assert np.array_equal(jv.jv_ilu0_factor(h, T(v)).cpu().numpy(), olu)
@@ -227,7 +227,7 @@ def test_er_corner_full_size(cfg, dtypes):
     c = W.config(cfg)
     rp, ci, v = c["rowptr"], c["colidx"], c["vals"]
     brp, bci, bv = reordered(rp, ci, v)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, er_corner=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, er_corner=True)
     info = check_corner_info(h, brp, bci, 1024)
     vb = jv.jv_permute_values(h, T(v))
     for dt in dtypes:
@@ -242,7 +242,7 @@ def test_hybrid_full_size_c2():
     c = W.config("c2")
     rp, ci, v = c["rowptr"], c["colidx"], c["vals"]
     n = len(rp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, mode="hybrid")
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, mode="hybrid")
     info = jv.jv_get_info(h)
     assert 1 < info["hybrid_launches"][0] < info["nlev"][0]
     olu, st, _ = O.ilu0(rp, ci, v)
@@ -265,9 +265,9 @@ def check_solve_corners(rp, ci, v, brp, bci, olu, mode, min_rows, seed):
     oracle; FP32 (every mix of b and x precisions) bit-exact with the
     sync-free path without corners."""
     n = len(brp) - 1
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, er_corner=True, mode=mode,
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, er_corner=True, mode=mode,
                       stage_min_rows=min_rows)
-    h0 = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True)
+    h0 = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True)
     info = jv.jv_get_info(h)
     diag = O.diag_ptr(brp, bci)
     b = W.rhs(n, 1, seed=seed)

@@ -39,7 +39,7 @@ def symmetrised(rp, ci):
 def test_sym_levels_match_oracle(case):
     _, rp, ci, _ = case
     srp, sci = symmetrised(rp, ci)
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, sym_levels=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, sym_levels=True)
     for which, upper in (("L", False), ("U", True), ("Ut", False), ("Lt", True)):
         nlev, ptr, rows, lev = jv.jv_get_levels(h, which)
         olev, onlev, optr, orows = O.level_sets(srp, sci, upper=upper)
@@ -81,7 +81,7 @@ def test_sym_levels_reorder_keeps_factors_of_nonsymmetric_patterns(case):
     n = len(rp) - 1
     srp, sci = symmetrised(rp, ci)
     assert not (np.array_equal(srp, rp) and np.array_equal(sci, ci))   # really nonsymmetric
-    h = jv.jv_analyze(T(rp), T(ci), exact_division=True, reorder=True, sym_levels=True)
+    h = jv.jv_analyze(T(rp), T(ci), exact=True, reorder=True, sym_levels=True)
     _, _, _, perm = O.level_sets(srp, sci)
     assert np.array_equal(jv.jv_get_perm(h)[0].cpu().numpy(), perm)
     iperm, brp, bci, vmap = O.permute(rp, ci, perm)
@@ -105,7 +105,7 @@ def test_sym_levels_reorder_keeps_factors_of_nonsymmetric_patterns(case):
 def test_sym_levels_band_rejected():
     rp, ci, _ = W.lap5(8)
     with pytest.raises(jv.JvError) as e:
-        jv.jv_analyze(T(rp), T(ci), exact_division=True, sym_levels=True, band_rows=64)
+        jv.jv_analyze(T(rp), T(ci), exact=True, sym_levels=True, band_rows=64)
     assert e.value.status == jv.JV_ERR_ARG
 
 
