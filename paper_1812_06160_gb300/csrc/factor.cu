@@ -208,28 +208,56 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
             if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
         }
-        unsigned char up[S];
-        TL sv[S];
+        if constexpr (S <= kLaneSlot) {
+            // the narrow slot: the pivots' positions, the update flags and the
+            // final-from-the-start operands as three batches of loads
+            unsigned char up[S];
+            TL sv[S];
 #pragma unroll
-        for (int e = 0; e < S; ++e) {
-            if (e < nl) kd[e] = __ldg(a.ppos + kd[e]);             // pivot row -> its position
-            if (e < np) up[e] = __ldg(a.upd + pr[e].y);
-        }
+            for (int e = 0; e < S; ++e) {
+                if (e < nl) kd[e] = __ldg(a.ppos + kd[e]);         // pivot row -> its position
+                if (e < np) up[e] = __ldg(a.upd + pr[e].y);
+            }
 #pragma unroll
-        for (int e = 0; e < S; ++e)
-            if (e < np && !up[e]) sv[e] = (TL)__ldg(vals + pr[e].y);  // u_kq = a_kq throughout
+            for (int e = 0; e < S; ++e)
+                if (e < np && !up[e]) sv[e] = (TL)__ldg(vals + pr[e].y);  // u_kq = a_kq throughout
 #pragma unroll
-        for (int e = 0; e < S; ++e) {
-            if (e < len) V(e) = v[e];
-            if (e < nl) { OPOS(e) = kd[e]; STEP_END(e) = (unsigned char)(se[e] - j0); }
-            if (e < np) {
-                OPOS(nl + e) = pr[e].y;
-                TGT(e) = (unsigned char)(pr[e].x - rs);
-                tmask |= 1u << (pr[e].x - rs);
-                if (!up[e]) {
-                    V(len + nl + e) = sv[e];
-                    smask |= 1u << (nl + e);
+            for (int e = 0; e < S; ++e) {
+                if (e < len) V(e) = v[e];
+                if (e < nl) { OPOS(e) = kd[e]; STEP_END(e) = (unsigned char)(se[e] - j0); }
+                if (e < np) {
+                    OPOS(nl + e) = pr[e].y;
+                    TGT(e) = (unsigned char)(pr[e].x - rs);
+                    tmask |= 1u << (pr[e].x - rs);
+                    if (!up[e]) {
+                        V(len + nl + e) = sv[e];
+                        smask |= 1u << (nl + e);
+                    }
                 }
+            }
+        } else {
+            // the wide slot: the row's arrays go to shared memory first and the
+            // dependent loads read them back, which keeps its registers in bounds
+#pragma unroll
+            for (int e = 0; e < S; ++e) {
+                if (e < len) V(e) = v[e];
+                if (e < nl) STEP_END(e) = (unsigned char)(se[e] - j0);
+                if (e < np) {
+                    OPOS(nl + e) = pr[e].y;
+                    TGT(e) = (unsigned char)(pr[e].x - rs);
+                    tmask |= 1u << (pr[e].x - rs);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < S; ++e) {
+                if (e < nl) kd[e] = __ldg(a.ppos + kd[e]);
+                if (e < np && !__ldg(a.upd + OPOS(nl + e))) smask |= 1u << (nl + e);
+            }
+#pragma unroll
+            for (int e = 0; e < S; ++e) {
+                if (e < nl) OPOS(e) = kd[e];
+                if (e < np && ((smask >> (nl + e)) & 1u))
+                    V(len + nl + e) = (TL)__ldg(vals + OPOS(nl + e));
             }
         }
         // a U entry no step updates is final already: store it now, so that
@@ -237,13 +265,11 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         // (no row awaits it: a reader takes it from A's values)
 #pragma unroll
         for (int e = 0; e < S; ++e)
-            if (e >= nl && e < len && !((tmask >> e) & 1u)) lu[rs + e] = v[e];
+            if (e >= nl && e < len && !((tmask >> e) & 1u)) lu[rs + e] = V(e);
         if (SF && gate) {               // bring the awaited operands' lines into L2 before sleeping
 #pragma unroll
-            for (int e = 0; e < S; ++e) {
-                if (e < nl) prefetch_l2(piv + kd[e]);
-                if (e < np && up[e]) prefetch_l2(lu + pr[e].y);
-            }
+            for (int e = 0; e < S; ++e)
+                if (e < m && !((smask >> e) & 1u)) prefetch_l2(src(e, OPOS(e)));
         }
     }
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
@@ -411,11 +437,15 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     if (fast) {
         for (int e = lane; e < np; e += G) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
         for (int e = lane; e < nl; e += G) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
-        for (int e0 = 0; e0 < m; e0 += G * kUnroll) {
-            int src[kUnroll];
-            U u[kUnroll];
+        // the operands, NB per lane at a time (the loads of a batch are issued
+        // together, then each is awaited): a group of 8 lanes takes 8 each, so
+        // that two batches cover 128 operands (a 27-point row has 114)
+        constexpr int NB = G == kWarp ? kUnroll : 2 * kUnroll;
+        for (int e0 = 0; e0 < m; e0 += G * NB) {
+            int src[NB];
+            U u[NB];
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k) {
+            for (int k = 0; k < NB; ++k) {
                 const int e = e0 + k * G + lane;
                 src[k] = -1;
                 if (e < m) {
@@ -434,7 +464,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
                 }
             }
 #pragma unroll
-            for (int k = 0; k < kUnroll; ++k)
+            for (int k = 0; k < NB; ++k)
                 if (src[k] != -1) {
                     const int e = e0 + k * G + lane;
                     if (SF && src[k] >= 0) u[k] = settle<TL>((e < nl ? piv : lu) + src[k], u[k], a, r, fail);

@@ -38,6 +38,34 @@ def close(got, want, rel=1e-12, floor_frac=1e-6):
     return not bad.any(), float((err / np.where(scale > 0, scale, 1.0)).max() if want.size else 0.0)
 
 
+def abs_factor(lu, diag):
+    """|L| and |U| for the absolute-value recurrences of solve_scale:
+    off-diagonal entries -|t|, diagonal |u_ii| (plain numpy)."""
+    out = -np.abs(np.asarray(lu, dtype=np.float64))
+    out[diag] = np.abs(np.asarray(lu, dtype=np.float64)[diag])
+    return out
+
+
+def solve_scale(solve, rowptr, colidx, diag, lu, b):
+    """Per-entry magnitude of a triangular solve's terms: the same solve
+    run on |b| with every off-diagonal entry -|t| and the diagonal |u_ii|, i.e.
+    s_r = (|b_r| + sum_j |t_rj| s_j) [/ |u_rr|].  A solve that adds its rows'
+    terms in another order (long rows summed by lanes and a tree) differs from
+    the serial one by rounding relative to s_r, and by that much only: the
+    componentwise bound of a triangular solve.  `solve` is the oracle's."""
+    return solve(rowptr, colidx, diag, abs_factor(lu, diag), np.abs(np.asarray(b, dtype=np.float64)))
+
+
+def close_scaled(got, want, scale, rel=1e-12):
+    """|g - o| <= rel * max(|o|, s) per entry, s from solve_scale."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    ref = np.maximum(np.abs(want), np.asarray(scale, dtype=np.float64))
+    err = np.abs(got - want)
+    worst = float((err / np.where(ref > 0, ref, 1.0)).max()) if want.size else 0.0
+    return not (err > rel * ref).any(), worst
+
+
 def max_rel(got, want):
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)

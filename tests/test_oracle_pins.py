@@ -663,3 +663,30 @@ def test_fgmres_solution_nonsymmetric():
     x, it, rel = O.fgmres(rp, ci, v, lu, b, m=30, tol=1e-10)
     assert it > 0 and rel <= 1e-10
     assert np.allclose(x, spla.spsolve(A.tocsc(), b), rtol=1e-8, atol=1e-9)
+
+
+def test_solve_scale_bounds_other_summation_orders():
+    # the scale the GPU tests measure tree-summed solve rows against: a
+    # forward substitution that adds each row's terms in another order (here
+    # reversed, in plain Python) stays within a few eps of the serial one
+    # relative to s = (|I - N|)^-1 |b|, even where the result itself cancels
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from jvutil import close_scaled, solve_scale
+    rp, ci, v = W.random_csr(300, 12.0, seed=91, dominant=False)
+    diag = O.diag_ptr(rp, ci)
+    lu, st, _ = O.ilu0(rp, ci, v, diag)
+    if st != O.OK:
+        lu = v.copy()
+    b = W.rhs(300, 1, seed=92)
+    x = O.lsolve(rp, ci, diag, lu, b)
+    y = np.zeros(300)
+    for r in range(300):
+        s = 0.0
+        for q in range(diag[r] - 1, rp[r] - 1, -1):
+            s += lu[q] * y[ci[q]]
+        y[r] = b[r] - s
+    scale = solve_scale(O.lsolve, rp, ci, diag, lu, b)
+    assert np.all(scale >= np.abs(x) * (1 - 1e-12))
+    ok, err = close_scaled(y, x, scale, rel=1e-13)
+    assert ok, err
