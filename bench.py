@@ -261,6 +261,9 @@ def parse_args(argv=None):
     ap.add_argument("--reorder", action="store_true")
     ap.add_argument("--band-rows", type=int, default=0, help="sync-free band size (0: none)")
     ap.add_argument("--milu", action="store_true", help="modified ILU(0) factor")
+    ap.add_argument("--exact", action="store_true",
+                    help="every FP64 result bit for bit the serial algorithm's (divisions, "
+                         "serial sums of long rows)")
     ap.add_argument("--sym-levels", action="store_true", help="levels of lower(A + A^T)")
     ap.add_argument("--fill-level", type=int, default=0,
                     help="ILU(k): factor on the level-k fill pattern (symbolic phase timed apart)")
@@ -316,6 +319,8 @@ def main(argv=None):
         config["band_rows"] = a.band_rows
     if a.milu:
         config["factor"] = "MILU(0)"
+    if a.exact:
+        config["arithmetic"] = "exact (serial order, divisions)"
     if a.sym_levels:
         config["levels"] = "lower(A+A^T)"
     if a.er_corner:
@@ -354,7 +359,7 @@ def main(argv=None):
     ci = torch.tensor(c["colidx"], device=dev)
     h = jv.jv_analyze(rp, ci, mode=a.mode, reorder=a.reorder, check=False,
                       band_rows=a.band_rows, milu=a.milu, sym_levels=a.sym_levels,
-                      er_corner=a.er_corner, stage_min_rows=a.stage_min_rows)
+                      er_corner=a.er_corner, stage_min_rows=a.stage_min_rows, exact=a.exact)
     info = jv.jv_get_info(h)
     # level statistics of the factor's DAG and of the U solve's
     for which in ("L", "U"):

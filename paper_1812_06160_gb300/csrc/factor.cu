@@ -437,39 +437,31 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     if (fast) {
         for (int e = lane; e < np; e += G) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
         for (int e = lane; e < nl; e += G) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
-        // the operands, NB per lane at a time (the loads of a batch are issued
-        // together, then each is awaited): a group of 8 lanes takes 8 each, so
-        // that two batches cover 128 operands (a 27-point row has 114)
-        constexpr int NB = G == kWarp ? kUnroll : 2 * kUnroll;
-        for (int e0 = 0; e0 < m; e0 += G * NB) {
-            int src[NB];
-            U u[NB];
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                const int e = e0 + k * G + lane;
-                src[k] = -1;
-                if (e < m) {
-                    if (e < nl) {                                  // the pivot of step e
-                        src[k] = __ldg(a.ppos + __ldg(a.colidx + rs + e));
-                        u[k] = first_read<TL, SF>(piv + src[k]);
-                    } else {                                       // u_kq of pair e - nl
-                        src[k] = __ldg(a.pairs + j0 + e - nl).y;
-                        if (__ldg(a.upd + src[k])) {
-                            u[k] = first_read<TL, SF>(lu + src[k]);
-                        } else {                                   // final from the start
-                            u[k] = B::to((TL)__ldg(vals + src[k]));
-                            src[k] = -2;
-                        }
-                    }
-                }
+        // the operands in two passes that keep no per-operand registers: the
+        // first issues every first read (independent loads, all in flight
+        // together) and parks the raw word in shared memory; the second
+        // awaits, in order, the words that still held the sentinel
+        auto where = [&](int e, bool &fixed) -> const TL * {
+            fixed = false;
+            if (e < nl) return piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));   // pivot of step e
+            const int q = __ldg(a.pairs + j0 + e - nl).y;                       // u_kq of a pair
+            if (__ldg(a.upd + q)) return lu + q;
+            fixed = true;                                  // final from the start: A's value
+            return reinterpret_cast<const TL *>(vals + q);
+        };
+#pragma unroll 4
+        for (int e = lane; e < m; e += G) {
+            bool fixed;
+            const TL *p = where(e, fixed);
+            uv[e] = fixed ? (TL)__ldg(reinterpret_cast<const TV *>(p)) : B::from(first_read<TL, SF>(p));
+        }
+        if (SF) {
+            for (int e = lane; e < m; e += G) {
+                if (B::to(uv[e]) != B::kSent) continue;
+                bool fixed;
+                const TL *p = where(e, fixed);
+                uv[e] = B::from(settle<TL>(p, B::kSent, a, r, fail));
             }
-#pragma unroll
-            for (int k = 0; k < NB; ++k)
-                if (src[k] != -1) {
-                    const int e = e0 + k * G + lane;
-                    if (SF && src[k] >= 0) u[k] = settle<TL>((e < nl ? piv : lu) + src[k], u[k], a, r, fail);
-                    uv[e] = B::from(u[k]);
-                }
         }
     }
     __syncwarp(gmask);
