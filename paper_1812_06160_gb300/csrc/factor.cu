@@ -439,8 +439,8 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         for (int e = lane; e < nl; e += G) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
         // the operands in two passes that keep no per-operand registers: the
         // first issues every first read (independent loads, all in flight
-        // together) and parks the raw word in shared memory; the second
-        // awaits, in order, the words that still held the sentinel
+        // together) and parks the value in shared memory; the second polls, in
+        // rounds, the words that still held the sentinel
         auto where = [&](int e, bool &fixed) -> const TL * {
             fixed = false;
             if (e < nl) return piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));   // pivot of step e
@@ -456,11 +456,38 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
             uv[e] = fixed ? (TL)__ldg(reinterpret_cast<const TV *>(p)) : B::from(first_read<TL, SF>(p));
         }
         if (SF) {
-            for (int e = lane; e < m; e += G) {
-                if (B::to(uv[e]) != B::kSent) continue;
-                bool fixed;
-                const TL *p = where(e, fixed);
-                uv[e] = B::from(settle<TL>(p, B::kSent, a, r, fail));
+            // rounds: every lane re-reads all its words still missing, the
+            // loads of a round in flight together, until the group has them all
+            // (bounded like every wait: the abort word, then the cycle budget)
+            long long t0 = 0;
+            unsigned rounds = 0;
+            bool pending = true;
+            while (__any_sync(gmask, pending)) {
+                if (pending) {
+                    pending = false;
+#pragma unroll 4
+                    for (int e = lane; e < m; e += G) {
+                        if (B::to(uv[e]) != B::kSent) continue;
+                        bool fixed;
+                        const U u = ld_relaxed(reinterpret_cast<const U *>(where(e, fixed)));
+                        if (u != B::kSent) uv[e] = B::from(u);
+                        else pending = true;
+                    }
+                    if (pending) {
+                        if (rounds++ == 0) t0 = clock64();
+                        if ((rounds & 15u) == 0) {
+                            if (sf_aborted(a.ticket)) {            // another wait gave up
+                                fail = true;
+                                pending = false;
+                            } else if (clock64() - t0 > a.timeout) {
+                                report(a.status, JV_ERR_TIMEOUT, r);
+                                sf_abort(a.ticket);
+                                fail = true;
+                                pending = false;
+                            }
+                        }
+                    }
+                }
             }
         }
     }

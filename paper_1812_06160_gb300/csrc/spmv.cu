@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict
                                                     const T *__restrict__ x, T *y, T alpha, T beta,
                                                     int has_alpha, int has_beta) {
     const long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
-    if (t >= n) return;
-    const int r = __ldg(srows + t);
-    const int p0 = __ldg(rowptr + r), p1 = __ldg(rowptr + r + 1);
+    // lanes past the last row take an empty row (they stay for the warp votes)
+    const int r = t < n ? __ldg(srows + t) : -1;
+    const int p0 = r >= 0 ? __ldg(rowptr + r) : 0, p1 = r >= 0 ? __ldg(rowptr + r + 1) : 0;
     int j2[U];
     T a1[U], x1[U], a2[U];
     // chunk 0: indices and values, then its gathers; chunk 1: indices and values
@@ -55,7 +55,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict
     for (int k = 0; k < U; ++k)
         if (p0 + U + k < p1) { j2[k] = __ldg(colidx + p0 + U + k); a2[k] = __ldg(vals + p0 + U + k); }
     T s = 0;
-    for (int c = p0; c < p1; c += U) {
+    // a warp-uniform trip count (the longest row of the warp): the warp votes
+    // in the loop need every lane
+    const int nch = __reduce_max_sync(0xffffffffu, (unsigned)((p1 - p0 + U - 1) / U));
+    for (int ci = 0, c = p0; ci < nch; ++ci, c += U) {
         T x2[U];
 #pragma unroll
         for (int k = 0; k < U; ++k)                       // gathers of chunk c+1
@@ -64,9 +67,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict
 #pragma unroll
         for (int k = 0; k < U; ++k)                       // indices and values of chunk c+2
             if (c + 2 * U + k < p1) { j2[k] = __ldg(colidx + c + 2 * U + k); a3[k] = __ldg(vals + c + 2 * U + k); }
+        // the chain of chunk c; the lanes' rows have about the same length, so
+        // the tail test is made warp-uniform first: an FP64 instruction whose
+        // lanes are all switched off still costs its 64 cycles of the pipe
 #pragma unroll
-        for (int k = 0; k < U; ++k)                       // the chain of chunk c
-            if (c + k < p1) s = RN<T>::fma(a1[k], x1[k], s);
+        for (int k = 0; k < U; ++k)
+            if (__any_sync(0xffffffffu, c + k < p1) && c + k < p1) s = RN<T>::fma(a1[k], x1[k], s);
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             a1[k] = a2[k];
@@ -74,6 +80,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict
             a2[k] = a3[k];
         }
     }
+    if (r < 0) return;
     T v = has_alpha ? RN<T>::mul(alpha, s) : s;            // alpha = 1: the product is s exactly
     if (has_beta) v = RN<T>::fma(beta, y[r], v);
     y[r] = v;
