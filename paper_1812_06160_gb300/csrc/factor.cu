@@ -302,15 +302,18 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     long long t0 = 0;
     unsigned rounds = 0;
     U u[W];
-    if (SF && __all_sync(0xffffffffu, done || m <= W)) {
-        // every operand of the row fits the window: each round polls only the
-        // operands not seen yet (a bit mask); the row is factored the round
-        // its last operand arrives
+    // operands past the window that must be awaited (the rest were read from
+    // A's values): none for MILU's 7-point rows, whose 9 pair operands all are
+    const unsigned need = m >= 32 ? 0xffffffffu : (1u << m) - 1u;
+    const unsigned late = W >= 32 ? 0u : ((need & ~smask) >> W);
+    if (SF && __all_sync(0xffffffffu, done || late == 0u)) {
+        // every awaited operand of the row fits the window: each round polls
+        // only the operands not seen yet (a bit mask); the row is factored the
+        // round its last operand arrives
         int op[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) op[k] = k < m ? OPOS(k) : 0;
         unsigned seen = smask;
-        const unsigned need = (1u << m) - 1u;
         while (__any_sync(0xffffffffu, !done)) {
 #pragma unroll
             for (int k = 0; k < W; ++k)
@@ -554,6 +557,141 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
     __syncwarp(gmask);                                         // shared memory reusable
 }
 
+// ------------------------------------------------- four rows per warp
+// The medium rows of a task (up to kWarp / kGroupLanes of one level), one
+// group of kGroupLanes lanes each, in lockstep: every loop runs the warp's
+// largest trip count and every barrier spans the warp, so the groups never
+// diverge and each FP64 warp instruction of the step loop serves all four
+// rows (groups whose row has fewer steps, or no row, sit the extra
+// iterations out).  Every row of such a task fits its group's share of the
+// warp's shared memory (the analysis checks it).
+template <class TV, class TL, bool SF, bool RCP>
+__device__ __forceinline__ void factor_group(const FactorArgs &a, int lo, int hi, unsigned gate,
+                                             unsigned char *smem, int share) {
+    using B = Bits<TL>;
+    using U = typename B::U;
+    constexpr int G = kGroupLanes;
+    const int lane = threadIdx.x & (G - 1);
+    const int g = (threadIdx.x & (kWarp - 1)) / G;
+    const unsigned gmask = ((1u << G) - 1u) << (g * G);
+    const int pos = lo + g;
+    const bool has = pos < hi;
+    int r = 0, rs = 0, len = 0, nl = 0, j0 = 0, np = 0;
+    if (has) {
+        r = __ldg(a.rows + pos);
+        rs = __ldg(a.rowptr + r);
+        len = __ldg(a.rowptr + r + 1) - rs;
+        const int rd = __ldg(a.diag + r);
+        nl = rd - rs;
+        j0 = __ldg(a.pair_ptr + rs);
+        np = __ldg(a.pair_ptr + rd) - j0;
+    }
+    const int m = nl + np;
+    bool fail = false;
+    TL *lu = static_cast<TL *>(a.lu);
+    TL *piv = static_cast<TL *>(a.piv);
+    const TV *vals = static_cast<const TV *>(a.vals);
+    TL *w = reinterpret_cast<TL *>(smem + g * share);
+    TL *uv = w + len;
+    int *tgt = reinterpret_cast<int *>(uv + m);
+    int *send = tgt + np;
+    for (int e = lane; e < len; e += G) w[e] = (TL)__ldg(vals + rs + e);
+    if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
+    for (int e = lane; e < np; e += G) tgt[e] = __ldg(a.pairs + j0 + e).x - rs;
+    for (int e = lane; e < nl; e += G) send[e] = __ldg(a.pair_ptr + rs + e + 1) - j0;
+    // operands: all first reads in flight together, then rounds over the
+    // words still missing (see factor_warp)
+    auto where = [&](int e, bool &fixed) -> const TL * {
+        fixed = false;
+        if (e < nl) return piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
+        const int q = __ldg(a.pairs + j0 + e - nl).y;
+        if (__ldg(a.upd + q)) return lu + q;
+        fixed = true;
+        return reinterpret_cast<const TL *>(vals + q);
+    };
+#pragma unroll 4
+    for (int e = lane; e < m; e += G) {
+        bool fixed;
+        const TL *p = where(e, fixed);
+        uv[e] = fixed ? (TL)__ldg(reinterpret_cast<const TV *>(p)) : B::from(first_read<TL, SF>(p));
+    }
+    if (SF) {
+        long long t0 = 0;
+        unsigned rounds = 0;
+        bool pending = true;
+        while (__any_sync(0xffffffffu, pending)) {
+            if (pending) {
+                pending = false;
+#pragma unroll 4
+                for (int e = lane; e < m; e += G) {
+                    if (B::to(uv[e]) != B::kSent) continue;
+                    bool fixed;
+                    const U u = ld_relaxed(reinterpret_cast<const U *>(where(e, fixed)));
+                    if (u != B::kSent) uv[e] = B::from(u);
+                    else pending = true;
+                }
+                if (pending) {
+                    if (rounds++ == 0) t0 = clock64();
+                    if ((rounds & 15u) == 0) {
+                        if (sf_aborted(a.ticket)) {
+                            fail = true;
+                            pending = false;
+                        } else if (clock64() - t0 > a.timeout) {
+                            report(a.status, JV_ERR_TIMEOUT, r);
+                            sf_abort(a.ticket);
+                            fail = true;
+                            pending = false;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // the steps, in lockstep across the groups
+    const int nlmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)nl);
+    int jb = 0;
+    for (int p = 0; p < nlmax; ++p) {
+        TL lik = 0;
+        int je = jb;
+        if (p < nl) {
+            lik = RCP ? w[p] * uv[p] : RN<TL>::div(w[p], uv[p]);
+            je = send[p];
+        }
+        const int cmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(je - jb));
+        for (int c = 0; c < cmax; c += G) {
+            const int j = jb + c + lane;
+            if (j < je) {
+                const int t = tgt[j];
+                if (!a.milu || t != nl) w[t] = RN<TL>::fms(lik, uv[nl + j], w[t]);
+            }
+        }
+        // MILU: several pairs of one step may target the diagonal (lane 0, in order)
+        if (a.milu && lane == 0)
+            for (int j = jb; j < je; ++j)
+                if (tgt[j] == nl) w[nl] = RN<TL>::fms(lik, uv[nl + j], w[nl]);
+        jb = je;
+        __syncwarp();
+        if (lane == 0 && p < nl) w[p] = lik;
+    }
+    __syncwarp();
+    const unsigned failed = __ballot_sync(0xffffffffu, fail);
+    if (has && !(SF && (failed & gmask))) {
+        if (lane == 0) pivot_check<TL>(a, r, w[nl]);
+        if (lane == 0 && (!SF || r != a.fault_row)) {
+            const TL pv = RCP ? rcp_newton(w[nl]) : w[nl];
+            if (SF) publish<TL>(piv + pos, pv);
+            else piv[pos] = pv;
+        }
+        for (int e = lane; e < len; e += G) {
+            const TL v = w[e];
+            if (!SF || e < nl) lu[rs + e] = v;
+            else if (r != a.fault_row) publish<TL>(lu + rs + e, v);
+        }
+    }
+    __syncwarp();                                              // shared memory reusable
+}
+
 // ------------------------------------------- one warp per row, pull form
 // Fig. 1's arithmetic regrouped by target: entry t of row r receives its
 // updates a_t -= l_p u_q (ascending step p, one fused multiply-add each) --
@@ -680,11 +818,9 @@ __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsig
             factor_warp_pull<TV, TL, SF, S, RCP>(a, lo, gate, smem);
         else
             factor_warp<TV, TL, SF, RCP, kWarp>(a, lo, gate, smem, warp_smem<S>());
-    } else if (hi & kGroupBit) {                 // kWarp / kGroupLanes rows, one per group
-        constexpr int share = warp_smem<S>() / (kWarp / kGroupLanes);
-        const int g = (threadIdx.x & (kWarp - 1)) / kGroupLanes;
-        if (lo + g < (hi & ~kGroupBit))
-            factor_warp<TV, TL, SF, RCP, kGroupLanes>(a, lo + g, gate, smem + g * share, share);
+    } else if (hi & kGroupBit) {                 // kWarp / kGroupLanes rows in lockstep
+        factor_group<TV, TL, SF, RCP>(a, lo, hi & ~kGroupBit, gate, smem,
+                                      warp_smem<S>() / (kWarp / kGroupLanes));
     }
     else factor_lanes<TV, TL, SF, W, S, RCP>(a, lo, hi, gate, smem);
     __syncwarp();
