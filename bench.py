@@ -365,7 +365,7 @@ def main(argv=None):
     for which in ("L", "U"):
         nl, lptr, _, _ = jv.jv_get_levels(h, which)
         w = np.diff(lptr.cpu().numpy())
-        config[f"levels_{which}"] = {"n": int(nl), "widest": int(w.max()),
+        config[f"levels_{which}"] = {"n": int(nl), "narrowest": int(w.min()), "widest": int(w.max()),
                                      "median": float(np.median(w))}
     if a.er_corner:
         t = 0 if a.dtype == "f64" else 1

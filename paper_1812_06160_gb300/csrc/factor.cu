@@ -301,6 +301,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
     };
     long long t0 = 0;
     unsigned rounds = 0;
+    unsigned held = 0;                  // FP64: rounds the warp's ready rows have waited
     U u[W];
     // operands past the window that must be awaited (the rest were read from
     // A's values): none for MILU's 7-point rows, whose 9 pair operands all are
@@ -332,7 +333,9 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                 // fused multiply-adds) costs the same with 1 or 32 lanes, so
                 // the rows wait until all rows of the warp are ready and
                 // finish together (C2 factor 1.50 -> 1.29 ms, C5 3.94 -> 3.72)
-                if (!__all_sync(0xffffffffu, done || ready)) go = false;
+                // -- for at most kHoldRounds rounds, so that a row held for
+                // a slow warp-mate never holds up its own dependants for long
+                if (!__all_sync(0xffffffffu, done || ready) && ++held <= kHoldRounds) go = false;
             }
             if (go) {
                 finish();
@@ -383,8 +386,8 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         bool go = ready;
         if constexpr (sizeof(TL) == 8) {
             // FP64: finish the warp's rows together, as in the single-window
-            // loop (C2 MILU(0) factor 3.12 -> 2.21 ms)
-            if (!__all_sync(0xffffffffu, done || ready)) go = false;
+            // loop (C2 MILU(0) factor 3.12 -> 2.21 ms), for a bounded time
+            if (!__all_sync(0xffffffffu, done || ready) && ++held <= kHoldRounds) go = false;
         }
         if (go) {
             finish();

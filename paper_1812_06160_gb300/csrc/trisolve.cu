@@ -224,8 +224,12 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
             // stores them together (C2 L and U solves 0.68 -> 0.63 ms; tasks
             // of 16 rows, on narrow levels, lost 2 % this way and keep the
             // per-row finish below)
+            // (for at most kHoldRounds rounds: then the rows finish one by
+            // one below, so that a row held for a slow warp-mate never holds
+            // up its own dependants for long)
             bool ready = done || len == 0;
-            for (;;) {
+            bool together = true;
+            for (unsigned held = 0;; ++held) {
 #pragma unroll
                 for (int k = 0; k < W; ++k)
                     if (!ready && k < len && !((seen >> k) & 1u)) u[k] = ld_relaxed(reinterpret_cast<const U *>(x + jw[k]));
@@ -234,6 +238,10 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                     if (!ready && k < len && !((seen >> k) & 1u) && u[k] != B::kSent) seen |= 1u << k;
                 ready = ready || seen == need;
                 if (__all_sync(0xffffffffu, ready)) break;
+                if (held >= kHoldRounds) {
+                    together = false;
+                    break;
+                }
                 if (!ready) {
                     if (rounds++ == 0) t0 = clock64();
                     if ((rounds & 15u) == 0) {
@@ -247,13 +255,15 @@ __device__ __forceinline__ void trsv_lanes(const TriArgs &a, int lo, int hi) {
                     }
                 }
             }
-            if (!done) {
+            if (together) {
+                if (!done) {
 #pragma unroll
-                for (int k = 0; k < W; ++k)
-                    if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
-                store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
+                    for (int k = 0; k < W; ++k)
+                        if (k < len) s = RN<TL>::fms(vw[k], (TL)B::from(u[k]), s);
+                    store_xp<TL, TX>(a, SF, pos, r, finish_row<TL>(a, s, d, dy));
+                }
+                return;
             }
-            return;
         }
         int e = 0;                                       // entries consumed (wide windows)
         while (__any_sync(0xffffffffu, !done)) {

@@ -131,10 +131,10 @@ def test_nonsymmetric_powerlaw_level_statistics():
             assert np.array_equal(rows.cpu().numpy(), orows)
             w = np.diff(optr)
             stats[("lower(A+A^T)" if sym else "lower(A)", which)] = (
-                onlev, int(w.max()), float(np.median(w)))
+                onlev, int(w.min()), int(w.max()), float(np.median(w)))
         lu = jv.jv_ilu0_factor(h, T(v)).cpu().numpy()
         ok, err = close(lu, olu)
         assert ok, (sym, err)
-    for k, (nl, mx, med) in stats.items():
-        print(f"{k[0]:>13} {k[1]}: {nl} levels, widest {mx} rows, median {med:.0f}")
+    for k, (nl, mn, mx, med) in stats.items():
+        print(f"{k[0]:>13} {k[1]}: {nl} levels, rows per level min {mn} max {mx} median {med:.0f}")
     assert stats[("lower(A+A^T)", "L")][0] >= stats[("lower(A)", "L")][0]
