@@ -198,17 +198,17 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
         const int np = __ldg(a.pair_ptr + rs + nl) - j0;
         m = nl + np;
         const TV *vals = static_cast<const TV *>(a.vals);
-        TL v[S];
-        int kd[S], se[S];
-        int2 pr[S];
-#pragma unroll
-        for (int e = 0; e < S; ++e) {
-            if (e < len) v[e] = (TL)__ldg(vals + rs + e);
-            if (e < nl) kd[e] = __ldg(a.colidx + rs + e);
-            if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
-            if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
-        }
         if constexpr (S <= kLaneSlot) {
+            TL v[S];
+            int kd[S], se[S];
+            int2 pr[S];
+#pragma unroll
+            for (int e = 0; e < S; ++e) {
+                if (e < len) v[e] = (TL)__ldg(vals + rs + e);
+                if (e < nl) kd[e] = __ldg(a.colidx + rs + e);
+                if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
+                if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
+            }
             // the narrow slot: the pivots' positions, the update flags and the
             // final-from-the-start operands as three batches of loads
             unsigned char up[S];
@@ -236,29 +236,42 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                 }
             }
         } else {
-            // the wide slot: the row's arrays go to shared memory first and the
-            // dependent loads read them back, which keeps its registers in bounds
+            // the wide slot: sixteen entries at a time through shared memory,
+            // and the dependent loads read the arrays back, which keeps the
+            // registers of the whole kernel (its poll loop included) in bounds
+            for (int h0 = 0; h0 < S; h0 += 16) {
+                TL v[16];
+                int kd[16], se[16];
+                int2 pr[16];
 #pragma unroll
-            for (int e = 0; e < S; ++e) {
-                if (e < len) V(e) = v[e];
-                if (e < nl) STEP_END(e) = (unsigned char)(se[e] - j0);
-                if (e < np) {
-                    OPOS(nl + e) = pr[e].y;
-                    TGT(e) = (unsigned char)(pr[e].x - rs);
-                    tmask |= 1u << (pr[e].x - rs);
+                for (int i = 0; i < 16; ++i) {
+                    const int e = h0 + i;
+                    if (e < len) v[i] = (TL)__ldg(vals + rs + e);
+                    if (e < nl) kd[i] = __ldg(a.colidx + rs + e);
+                    if (e < nl) se[i] = __ldg(a.pair_ptr + rs + e + 1);
+                    if (e < np) pr[i] = __ldg(a.pairs + j0 + e);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int e = h0 + i;
+                    if (e < len) V(e) = v[i];
+                    if (e < nl) { OPOS(e) = kd[i]; STEP_END(e) = (unsigned char)(se[i] - j0); }
+                    if (e < np) {                          // pair slots lie above every step slot
+                        OPOS(nl + e) = pr[i].y;
+                        TGT(e) = (unsigned char)(pr[i].x - rs);
+                        tmask |= 1u << (pr[i].x - rs);
+                    }
                 }
             }
-#pragma unroll
+#pragma unroll 8
             for (int e = 0; e < S; ++e) {
-                if (e < nl) kd[e] = __ldg(a.ppos + kd[e]);
+                if (e < nl) OPOS(e) = __ldg(a.ppos + OPOS(e));    // pivot row -> its position
                 if (e < np && !__ldg(a.upd + OPOS(nl + e))) smask |= 1u << (nl + e);
             }
-#pragma unroll
-            for (int e = 0; e < S; ++e) {
-                if (e < nl) OPOS(e) = kd[e];
+#pragma unroll 8
+            for (int e = 0; e < S; ++e)
                 if (e < np && ((smask >> (nl + e)) & 1u))
                     V(len + nl + e) = (TL)__ldg(vals + OPOS(nl + e));
-            }
         }
         // a U entry no step updates is final already: store it now, so that
         // only the updated ones (for a stencil, the diagonal) follow the steps
