@@ -23,6 +23,7 @@ constexpr int kLongDeps = 24;     // solve rows with more dependencies run one p
 constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
 constexpr int kLaneSlotWide = 32; // the same, when many rows need 17..32 (e.g. MILU fill pairs)
 constexpr unsigned kHoldRounds = 64; // FP64 factor: poll rounds a ready row waits for its warp-mates
+constexpr int kSpmvStage = 256;    // spmv: entries a warp stages in shared memory
 
 // ---------------------------------------------------------------- launches
 extern std::atomic<unsigned long long> g_launches;
