@@ -194,7 +194,8 @@ __global__ void k_tpairs(int np, const unsigned *sorted_idx, const unsigned *ste
 // pull form pays -- its waves (= that depth) at most half the row's steps.
 // depth[] is scratch over the row's positions.  One thread per row.
 __global__ void k_row_pull(int n, const int *rowptr, const int *diag, const int *tpair_ptr,
-                           const int2 *tpairs, int *depth, unsigned char *pull) {
+                           const int2 *tpairs, int *depth, unsigned char *pull,
+                           unsigned char *edepth) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int rs = rowptr[r], rd = diag[r];
@@ -203,6 +204,7 @@ __global__ void k_row_pull(int n, const int *rowptr, const int *diag, const int 
         int d = 1;
         for (int k = tpair_ptr[p]; k < tpair_ptr[p + 1]; ++k) d = max(d, depth[tpairs[k].x] + 1);
         depth[p] = d;
+        edepth[p] = (unsigned char)min(d, 255);
         most = max(most, d);
     }
     pull[r] = (unsigned char)(2 * most <= rd - rs ? 1 : 0);
@@ -610,13 +612,14 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
         JV_CUDA(cudaMemsetAsync(h->tpair_ptr, 0, ((size_t)nnz + 1) * 4, s));
     }
     JV_TRY(halloc_n(h, &h->row_pull, n));
+    JV_TRY(halloc_n(h, &h->edepth, nnz));
     {
         Temp dtmp;
         int *depth;
         JV_TRY(dtmp.get(&depth, nnz));
         count_launch();
         k_row_pull<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, h->diag, h->tpair_ptr,
-                                                          h->tpairs, depth, h->row_pull);
+                                                          h->tpairs, depth, h->row_pull, h->edepth);
         JV_CHECK_LAUNCH();
         JV_CUDA(cudaStreamSynchronize(s));
     }

@@ -89,6 +89,7 @@ struct FactorArgs {
     void *pscratch;               // operands of rows too long for shared memory
     long long npairs_total;       // offset of the u_kk area in pscratch
     const unsigned char *row_pull; // per row: take the pull form
+    const unsigned char *edepth;  // per L entry: depth of its in-row chain (255: 255 or more)
     const int *colidx;            // column of every entry: the pivot row k of entry (r, k)
     const int *ppos;              // work-list position of every row (where its pivot is published)
     const unsigned char *upd;     // 1: some step updates the entry (a pair operand to await)
@@ -775,33 +776,53 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
         }
     }
     __syncwarp();
-    // L entries: chunks of 32, waves inside a chunk
-    for (int c0 = 0; c0 < nl; c0 += kWarp) {
-        const int e = c0 + lane;
-        int t0 = 0, t1 = 0;
-        bool done = e >= nl;
-        if (!done) {
-            t0 = __ldg(a.tpair_ptr + rs + e) - s0;
-            t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
-        }
-        for (unsigned dm = __ballot_sync(0xffffffffu, done); dm != 0xffffffffu;
-             dm = __ballot_sync(0xffffffffu, done)) {
-            bool ready = !done;
-            for (int k = t0; k < t1 && ready; ++k) {
-                const int pp = __ldg(a.tpairs + s0 + k).x - rs - c0;
-                if (pp >= 0) ready = (dm >> pp) & 1u;          // a producer in this chunk
-            }
-            if (ready) {
-                TL acc = w[e];
-                for (int k = t0; k < t1; ++k)
-                    acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
-                w[e] = RCP ? acc * ukk[e] : RN<TL>::div(acc, ukk[e]);
-                done = true;
-            }
+    // one L entry: its updates in ascending step, then the division
+    auto finish_l = [&](int e) {
+        const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
+        TL acc = w[e];
+        for (int k = t0; k < t1; ++k) acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
+        w[e] = RCP ? acc * ukk[e] : RN<TL>::div(acc, ukk[e]);
+    };
+    // L entries by depth of their in-row chain (the analysis's edepth: an
+    // entry's producers all have smaller depth), every entry of one depth at
+    // once, lane-strided with four entries in flight per lane; a row whose
+    // chain is 255 deep or more takes chunks of 32 with waves inside a chunk
+    int dmax = 0;
+    for (int e = lane; e < nl; e += kWarp) dmax = max(dmax, (int)__ldg(a.edepth + rs + e));
+    dmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)dmax);
+    if (dmax < 255) {
+        for (int d = 1; d <= dmax; ++d) {
+#pragma unroll 4
+            for (int e = lane; e < nl; e += kWarp)
+                if (dmax == 1 || __ldg(a.edepth + rs + e) == d) finish_l(e);
             __syncwarp();
+        }
+    } else {
+        for (int c0 = 0; c0 < nl; c0 += kWarp) {
+            const int e = c0 + lane;
+            int t0 = 0, t1 = 0;
+            bool done = e >= nl;
+            if (!done) {
+                t0 = __ldg(a.tpair_ptr + rs + e) - s0;
+                t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
+            }
+            for (unsigned dm = __ballot_sync(0xffffffffu, done); dm != 0xffffffffu;
+                 dm = __ballot_sync(0xffffffffu, done)) {
+                bool ready = !done;
+                for (int k = t0; k < t1 && ready; ++k) {
+                    const int pp = __ldg(a.tpairs + s0 + k).x - rs - c0;
+                    if (pp >= 0) ready = (dm >> pp) & 1u;      // a producer in this chunk
+                }
+                if (ready) {
+                    finish_l(e);
+                    done = true;
+                }
+                __syncwarp();
+            }
         }
     }
     // U entries (the diagonal included): every one pulls its updates
+#pragma unroll 4
     for (int e = nl + lane; e < len; e += kWarp) {
         const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
         TL acc = w[e];
@@ -997,6 +1018,7 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.pscratch = h->pscratch;
     a.npairs_total = h->npairs;
     a.row_pull = h->row_pull;
+    a.edepth = h->edepth;
     a.colidx = h->colidx;
     a.ppos = W.ipos;
     a.upd = h->upd;

@@ -23,7 +23,6 @@ constexpr int kLongDeps = 24;     // solve rows with more dependencies run one p
 constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
 constexpr int kLaneSlotWide = 32; // the same, when many rows need 17..32 (e.g. MILU fill pairs)
 constexpr unsigned kHoldRounds = 64; // FP64 factor: poll rounds a ready row waits for its warp-mates
-constexpr int kSpmvStage = 256;    // spmv: entries a warp stages in shared memory
 
 // ---------------------------------------------------------------- launches
 extern std::atomic<unsigned long long> g_launches;
@@ -450,6 +449,8 @@ struct jv_handle_s {
     int *tpair_ptr = nullptr;                // [nnz + 1] the pairs grouped by target entry t:
     int2 *tpairs = nullptr;                  // [npairs] (p, q) -- step p, operand q -- ascending p
     unsigned char *row_pull = nullptr;       // [n] 1: a one-warp row takes the pull form
+    unsigned char *edepth = nullptr;         // [nnz] L entries: depth of the in-row chain of steps
+                                             // that update the entry (1: none; capped at 255)
     unsigned char *upd = nullptr;            // [nnz] 1: some step of the factor updates the entry
     long long ndyn_pairs = 0;                // pairs whose operand is updated (must be awaited)
     long long npairs = 0;

@@ -30,8 +30,7 @@ template <> struct RN<float> {
 // start first.  A lane streams its row in chunks of U entries through a
 // three-stage pipeline -- indices and values of chunk c+2 loading, x of chunk
 // c+1 being gathered, chunk c being summed -- so a long row's loads stay
-// ahead of its chain.  (Warps of 32 consecutive rows take the staged path
-// below instead.)
+// ahead of its chain.
 template <class T, int U>
 __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict__ srows,
                                                     const int *__restrict__ rowptr,
@@ -40,37 +39,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict
                                                     const T *__restrict__ x, T *y, T alpha, T beta,
                                                     int has_alpha, int has_beta) {
     const long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
-    const int lane = threadIdx.x & (kWarp - 1);
     // lanes past the last row take an empty row (they stay for the warp votes)
     const int r = t < n ? __ldg(srows + t) : -1;
     const int p0 = r >= 0 ? __ldg(rowptr + r) : 0, p1 = r >= 0 ? __ldg(rowptr + r + 1) : 0;
-    // Staged: when the warp's 32 rows are consecutive (rows of one length,
-    // e.g. the interior of a stencil, stay in their order), their entries are
-    // one contiguous range, read with coalesced loads into shared memory
-    // together with the gathered x_j; every lane then sums its row from there
-    // in the same serial order.
-    __shared__ T stage[kWarpsPerBlock][2][kSpmvStage];
-    const int rf = __shfl_sync(0xffffffffu, r, 0);
-    const int P0 = __shfl_sync(0xffffffffu, p0, 0), P1 = __shfl_sync(0xffffffffu, p1, kWarp - 1);
-    if (__all_sync(0xffffffffu, r >= 0 && r == rf + lane) && P1 - P0 <= kSpmvStage) {
-        T *sa = stage[threadIdx.x >> 5][0], *sx = stage[threadIdx.x >> 5][1];
-        const int m = P1 - P0;
-#pragma unroll 8
-        for (int e = lane; e < m; e += kWarp) {
-            sa[e] = __ldg(vals + P0 + e);
-            sx[e] = __ldg(x + __ldg(colidx + P0 + e));
-        }
-        __syncwarp();
-        const int q0 = p0 - P0, len = p1 - p0;
-        const int lmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
-        T s = 0;
-        for (int k = 0; k < lmax; ++k)
-            if (__any_sync(0xffffffffu, k < len) && k < len) s = RN<T>::fma(sa[q0 + k], sx[q0 + k], s);
-        T v = has_alpha ? RN<T>::mul(alpha, s) : s;
-        if (has_beta) v = RN<T>::fma(beta, y[r], v);
-        y[r] = v;
-        return;
-    }
     int j2[U];
     T a1[U], x1[U], a2[U];
     // chunk 0: indices and values, then its gathers; chunk 1: indices and values
