@@ -666,15 +666,15 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     h->fslot = 4 * mid_rows >= n ? kLaneSlotWide : kLaneSlot;
     // rows above the one-lane slot that fit a group's share of the warp's
     // shared memory (values and operands at 8 bytes, targets and step ends at
-    // 4), and whose L entries depend on each other (the pull form, for the
-    // others, spreads a row over the whole warp): kGroupLanes lanes each
-    std::vector<unsigned char> pull((size_t)n), grp((size_t)n, 0);
-    JV_CUDA(cudaMemcpyAsync(pull.data(), h->row_pull, (size_t)n, cudaMemcpyDeviceToHost, s));
-    JV_CUDA(cudaStreamSynchronize(s));
+    // 4): kGroupLanes lanes each, four rows to a warp in lockstep.  (One row
+    // per warp for these -- the pull form, for rows whose L entries are
+    // mostly independent -- kept the 40,000-row levels of the power-law matrix
+    // to 1,216 rows in flight.)  Longer rows keep the whole warp.
+    std::vector<unsigned char> grp((size_t)n, 0);
     const long long gcap = (long long)factor_warp_smem(h->fslot) / (kWarp / kGroupLanes);
     for (int i = 0; i < n; ++i) {
         const long long c = cost[4 * (size_t)n + i], len = hrp[i + 1] - hrp[i];
-        grp[i] = (unsigned char)(!pull[i] && c * 8 + (c - len) * 4 <= gcap);
+        grp[i] = (unsigned char)(c * 8 + (c - len) * 4 <= gcap);
     }
     JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, h->fslot, fops.data(),
                      h->fbins, grp.data()));
