@@ -394,15 +394,14 @@ int make_bins(jv_handle h, const LevelSet &L, const int *cost, int threshold, co
             lo.push_back(first + t);
             hi.push_back(first + std::min(t + per_task, nshort));
         }
-        for (int kind = 1; group && kind <= 2; ++kind) {   // step form, then pull form
+        if (group) {
             const int gfirst = (int)brows.size();
             for (int t = a; t < e; ++t)
-                if (cost[rows[t]] > threshold && group[rows[t]] == kind) brows.push_back(rows[t]);
+                if (cost[rows[t]] > threshold && group[rows[t]]) brows.push_back(rows[t]);
             const int ng = (int)brows.size() - gfirst;
             for (int t = 0; t < ng; t += kWarp / kGroupLanes) {
                 lo.push_back(gfirst + t);
-                hi.push_back((gfirst + std::min(t + kWarp / kGroupLanes, ng)) | kGroupBit |
-                             (kind == 2 ? kPullBit : 0));
+                hi.push_back((gfirst + std::min(t + kWarp / kGroupLanes, ng)) | kGroupBit);
                 ++B.ngroup;
             }
         }
@@ -667,11 +666,12 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     h->fslot = 4 * mid_rows >= n ? kLaneSlotWide : kLaneSlot;
     // rows above the one-lane slot that fit a group's share of the warp's
     // shared memory (values and operands at 8 bytes, targets and step ends at
-    // 4): kGroupLanes lanes each, four rows to a warp in lockstep, in the step
-    // form (1) or, for rows whose L entries are mostly independent, the pull
-    // form (2).  (One row per warp for the latter kept the 40,000-row levels
-    // of the power-law matrix to 1,216 rows in flight, and the step form
-    // walks its 16 steps one by one.)  Longer rows keep the whole warp.
+    // 4), and whose L entries depend on each other: kGroupLanes lanes each,
+    // four rows to a warp in lockstep.  Rows whose L entries are mostly
+    // independent take the pull form on the whole warp: on the power-law
+    // matrix four rows of unequal lengths per warp, in the step form or in the
+    // pull form, measured 13.4 -> 18.1 ms (FP64 factor), the lockstep loops
+    // running at the longest row's length.  Longer rows keep the whole warp.
     std::vector<unsigned char> pull((size_t)n);
     JV_CUDA(cudaMemcpyAsync(pull.data(), h->row_pull, (size_t)n, cudaMemcpyDeviceToHost, s));
     JV_CUDA(cudaStreamSynchronize(s));
@@ -679,7 +679,7 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     const long long gcap = (long long)factor_warp_smem(h->fslot) / (kWarp / kGroupLanes);
     for (int i = 0; i < n; ++i) {
         const long long c = cost[4 * (size_t)n + i], len = hrp[i + 1] - hrp[i];
-        if (c * 8 + (c - len) * 4 <= gcap) grp[i] = pull[i] ? 2 : 1;
+        grp[i] = (unsigned char)(!pull[i] && c * 8 + (c - len) * 4 <= gcap);
     }
     JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, h->fslot, fops.data(),
                      h->fbins, grp.data()));

@@ -719,139 +719,6 @@ __device__ __forceinline__ void factor_group(const FactorArgs &a, int lo, int hi
     __syncwarp();                                              // shared memory reusable
 }
 
-// ------------------------------------- four rows per warp, pull form
-// The pull form (below) for the medium rows of a task, one group of
-// kGroupLanes lanes per row, in lockstep like factor_group: the operands
-// (pivots, then the pair operands in target order), the L entries by the
-// depth of their in-row chain, then every U entry pulling its updates, each
-// loop at the warp's largest trip count.  The rows' arrays (values, u_kk,
-// u_q) fit the group's share of the warp's shared memory.
-template <class TV, class TL, bool SF, bool RCP>
-__device__ __forceinline__ void factor_group_pull(const FactorArgs &a, int lo, int hi, unsigned gate,
-                                                  unsigned char *smem, int share) {
-    using B = Bits<TL>;
-    using U = typename B::U;
-    constexpr int G = kGroupLanes;
-    const int lane = threadIdx.x & (G - 1);
-    const int g = (threadIdx.x & (kWarp - 1)) / G;
-    const unsigned gmask = ((1u << G) - 1u) << (g * G);
-    const int pos = lo + g;
-    const bool has = pos < hi;
-    int r = 0, rs = 0, len = 0, nl = 0, s0 = 0, nq = 0;
-    if (has) {
-        r = __ldg(a.rows + pos);
-        rs = __ldg(a.rowptr + r);
-        const int re = __ldg(a.rowptr + r + 1);
-        len = re - rs;
-        nl = __ldg(a.diag + r) - rs;
-        s0 = __ldg(a.tpair_ptr + rs);
-        nq = __ldg(a.tpair_ptr + re) - s0;
-    }
-    const int m = nl + nq;
-    bool fail = false;
-    TL *lu = static_cast<TL *>(a.lu);
-    TL *piv = static_cast<TL *>(a.piv);
-    const TV *vals = static_cast<const TV *>(a.vals);
-    TL *w = reinterpret_cast<TL *>(smem + g * share);
-    TL *ukk = w + len;                 // then u_q: ukk[nl + k] is the operand of tpair k
-    for (int e = lane; e < len; e += G) w[e] = (TL)__ldg(vals + rs + e);
-    if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
-    auto where = [&](int e, bool &fixed) -> const TL * {
-        fixed = false;
-        if (e < nl) return piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
-        const int q = __ldg(a.tpairs + s0 + e - nl).y;
-        if (__ldg(a.upd + q)) return lu + q;
-        fixed = true;
-        return reinterpret_cast<const TL *>(vals + q);
-    };
-#pragma unroll 4
-    for (int e = lane; e < m; e += G) {
-        bool fixed;
-        const TL *p = where(e, fixed);
-        ukk[e] = fixed ? (TL)__ldg(reinterpret_cast<const TV *>(p)) : B::from(first_read<TL, SF>(p));
-    }
-    if (SF) {
-        long long t0 = 0;
-        unsigned rounds = 0;
-        for (int ph = 0; ph < 2; ++ph) {                // pivots first, as in factor_group
-            bool pending = !fail;
-            while (__any_sync(0xffffffffu, pending)) {
-                if (pending) {
-                    pending = false;
-#pragma unroll 4
-                    for (int e = lane; e < (ph ? m : nl); e += G) {
-                        if (B::to(ukk[e]) != B::kSent) continue;
-                        bool fixed;
-                        const U u = ld_relaxed(reinterpret_cast<const U *>(where(e, fixed)));
-                        if (u != B::kSent) ukk[e] = B::from(u);
-                        else pending = true;
-                    }
-                    if (pending) {
-                        if (rounds++ == 0) t0 = clock64();
-                        if ((rounds & 15u) == 0) {
-                            if (sf_aborted(a.ticket)) {
-                                fail = true;
-                                pending = false;
-                            } else if (clock64() - t0 > a.timeout) {
-                                report(a.status, JV_ERR_TIMEOUT, r);
-                                sf_abort(a.ticket);
-                                fail = true;
-                                pending = false;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-    }
-    __syncwarp();
-    const TL *uq = ukk + nl;
-    // the L entries by depth, then the U entries; loops at the warp's largest
-    // trip count, so that every barrier spans the warp
-    int dmax = 0;
-    for (int e = lane; e < nl; e += G) dmax = max(dmax, (int)__ldg(a.edepth + rs + e));
-    dmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)dmax);
-    const int nlmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)nl);
-    for (int d = 1; d <= dmax; ++d) {
-        for (int c = 0; c < nlmax; c += G) {
-            const int e = c + lane;
-            if (e < nl && (dmax == 1 || __ldg(a.edepth + rs + e) == d)) {
-                const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
-                TL acc = w[e];
-                for (int k = t0; k < t1; ++k) acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
-                w[e] = RCP ? acc * ukk[e] : RN<TL>::div(acc, ukk[e]);
-            }
-        }
-        __syncwarp();
-    }
-    const int numax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(len - nl));
-    for (int c = 0; c < numax; c += G) {
-        const int e = nl + c + lane;
-        if (e < len) {
-            const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
-            TL acc = w[e];
-            for (int k = t0; k < t1; ++k) acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
-            w[e] = acc;
-        }
-    }
-    __syncwarp();
-    const unsigned failed = __ballot_sync(0xffffffffu, fail);
-    if (has && !(SF && (failed & gmask))) {
-        if (lane == 0) pivot_check<TL>(a, r, w[nl]);
-        if (lane == 0 && (!SF || r != a.fault_row)) {
-            const TL pv = RCP ? rcp_newton(w[nl]) : w[nl];
-            if (SF) publish<TL>(piv + pos, pv);
-            else piv[pos] = pv;
-        }
-        for (int e = lane; e < len; e += G) {
-            const TL v = w[e];
-            if (!SF || e < nl) lu[rs + e] = v;
-            else if (r != a.fault_row) publish<TL>(lu + rs + e, v);
-        }
-    }
-    __syncwarp();                                              // shared memory reusable
-}
-
 // ------------------------------------------- one warp per row, pull form
 // Fig. 1's arithmetic regrouped by target: entry t of row r receives its
 // updates a_t -= l_p u_q (ascending step p, one fused multiply-add each) --
@@ -999,11 +866,8 @@ __device__ __forceinline__ void factor_task(const FactorArgs &a, int task, unsig
         else
             factor_warp<TV, TL, SF, RCP, kWarp>(a, lo, gate, smem, warp_smem<S>());
     } else if (hi & kGroupBit) {                 // kWarp / kGroupLanes rows in lockstep
-        constexpr int share = warp_smem<S>() / (kWarp / kGroupLanes);
-        if (hi & kPullBit)
-            factor_group_pull<TV, TL, SF, RCP>(a, lo, hi & ~(kGroupBit | kPullBit), gate, smem, share);
-        else
-            factor_group<TV, TL, SF, RCP>(a, lo, hi & ~kGroupBit, gate, smem, share);
+        factor_group<TV, TL, SF, RCP>(a, lo, hi & ~kGroupBit, gate, smem,
+                                      warp_smem<S>() / (kWarp / kGroupLanes));
     }
     else factor_lanes<TV, TL, SF, W, S, RCP>(a, lo, hi, gate, smem);
     __syncwarp();

@@ -316,7 +316,6 @@ __device__ __forceinline__ int find_col(const int *__restrict__ col, int lo, int
 // the rows of a task never depend on each other.
 constexpr int kLongBit = (int)0x80000000u;   // task_hi flag: one-row cooperative task
 constexpr int kGroupBit = 0x40000000;        // task_hi flag (factor): rows of kGroupLanes lanes each
-constexpr int kPullBit = 0x20000000;         // with kGroupBit: the rows take the pull form
 constexpr int kGroupLanes = 8;
 struct Bins {
     int *rows = nullptr;       // [n] binned rows
