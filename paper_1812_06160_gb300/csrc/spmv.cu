@@ -30,9 +30,12 @@ template <> struct RN<float> {
 // start first.  A lane streams its row in chunks of U entries through a
 // three-stage pipeline -- indices and values of chunk c+2 loading, x of chunk
 // c+1 being gathered, chunk c being summed -- so a long row's loads stay
-// ahead of its chain.
-template <class T, int U>
-__global__ void __launch_bounds__(kBlock, 4) k_spmv(int n, const int *__restrict__ srows,
+// ahead of its chain.  FP64 matrices whose rows are all short (at most 32
+// entries) take chunks of 2 and six CTAs per SM (fewer registers, more warps
+// to hide the gathers: 7-point 128^3 spmv 68 -> 52 us); longer rows take
+// chunks of 4 and four CTAs per SM (the power-law matrix: 0.80 -> 0.62 ms).
+template <class T, int U, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_spmv(int n, const int *__restrict__ srows,
                                                     const int *__restrict__ rowptr,
                                                     const int *__restrict__ colidx,
                                                     const T *__restrict__ vals,
@@ -156,12 +159,17 @@ int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, doub
     const int grid = grid_for(h->n, kBlock);
     const int hb = beta != 0.0, ha = alpha != 1.0;
     count_launch();
-    if (t == JV_F64)
-        k_spmv<double, 4><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
-                                                          (const double *)vals, (const double *)x,
-                                                          (double *)y, alpha, beta, ha, hb);
-    else if (t == JV_F32)
-        k_spmv<float, 8><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
+    if (t == JV_F64) {
+        if (h->maxrow <= 32)
+            k_spmv<double, 2, 6><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
+                                                                 (const double *)vals, (const double *)x,
+                                                                 (double *)y, alpha, beta, ha, hb);
+        else
+            k_spmv<double, 4, 4><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
+                                                                 (const double *)vals, (const double *)x,
+                                                                 (double *)y, alpha, beta, ha, hb);
+    } else if (t == JV_F32)
+        k_spmv<float, 8, 4><<<grid, kBlock, 0, h->stream>>>(h->n, h->spmv_rows, h->rowptr, h->colidx,
                                                          (const float *)vals, (const float *)x,
                                                          (float *)y, (float)alpha, (float)beta, ha, hb);
     else
