@@ -54,9 +54,9 @@ KERNEL_SOURCES = {"factor": ("factor.cu", "jv_internal.cuh"),
                   "lsolve": ("trisolve.cu", "jv_internal.cuh"),
                   "usolve": ("trisolve.cu", "jv_internal.cuh")}
 TRAFFIC = {
-    ("c2", "f64", "factor", "syncfree", False): (537_112_832, "fe727fecab13"),
-    ("c2", "f64", "lsolve", "syncfree", False): (252_362_752, "df9c463a9e01"),
-    ("c2", "f64", "usolve", "syncfree", False): (253_896_960, "df9c463a9e01"),
+    ("c2", "f64", "factor", "syncfree", False): (471_790_336, "1680f0e4d5d7"),
+    ("c2", "f64", "lsolve", "syncfree", False): (265_703_424, "e2a12b5e2481"),
+    ("c2", "f64", "usolve", "syncfree", False): (268_858_112, "e2a12b5e2481"),
 }
 
 
