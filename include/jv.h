@@ -251,9 +251,14 @@ int jv_set_check(jv_handle h, int check);
  * (dtype lu_t) receives L (strictly lower part, unit diagonal implied) and U
  * (diagonal and strictly upper part) in the same pattern.  lu == vals is
  * allowed when the dtypes match (in place); vals_t = F64 with lu_t = F32
- * fuses the down-cast.  Arithmetic is done in lu_t with every product and
- * difference rounded separately, in the order of Fig. 1.  The pivot test
- * (u_ii == 0 or not finite -> JV_ERR_ZERO_PIVOT) is done in double.
+ * fuses the down-cast.  Arithmetic is done in lu_t, in the order of Fig. 1:
+ * every update a_ij -= l_ik u_kj is one fused multiply-add; the multiplier
+ * l_ik is the division a_ik / u_kk (FP32, or FP64 with options.exact = 1) or,
+ * by default in FP64, a_ik times the pivot's reciprocal (see
+ * jv_options.exact).  The pivot test (u_ii == 0 or not finite ->
+ * JV_ERR_ZERO_PIVOT) is done in double.  Device scratch (the pivot array,
+ * the work area of rows too long for shared memory) is allocated on the
+ * first call that needs it and kept by the handle.
  * bad_row (host, may be NULL): the smallest failing row, or -1. */
 int jv_ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals,
                    jv_dtype lu_t, void *lu, int *bad_row);
@@ -261,7 +266,12 @@ int jv_ilu0_factor(jv_handle h, jv_dtype vals_t, const void *vals,
 /* Forward substitution with the unit lower factor (Sec. VI, stri):
  * x = L^-1 b.  lu: factor from jv_ilu0_factor (dtype lu_t, which is also the
  * arithmetic type).  b (dtype b_t) and x (dtype x_t) are n x nrhs row-major,
- * nrhs >= 1; x must not overlap b. */
+ * nrhs >= 1; x must not overlap b.  Every row sums its terms in the serial
+ * order (ascending columns), one fused multiply-add each -- except, by
+ * default, a one-column row with more dependencies than options.long_row,
+ * which sums by lanes and a fixed tree (jv_options.exact).  A one-column
+ * solve keeps a handle-owned copy of x (allocated on first use) that its
+ * rows poll. */
 int jv_lsolve(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t,
               const void *b, jv_dtype x_t, void *x, int nrhs);
 
