@@ -173,6 +173,12 @@ typedef struct {
                                        the division's own result, the one-lane solve rows
                                        and the factor's other arithmetic keep the serial
                                        order, and FP32 divides (its pipe is full width). */
+    int spmv_long_row;              /* with exact = 0, spmv rows longer than this split their
+                                       sum over the 32 lanes of a warp (each lane's share in
+                                       ascending column order, then a fixed tree; the
+                                       result is deterministic run to run); shorter rows,
+                                       and every row with exact = 1, sum in the serial
+                                       order, one row per lane.  0 = default (128). */
 } jv_options;
 
 typedef struct {
@@ -195,6 +201,7 @@ typedef struct {
     int corner_levels[2];       /* levels of lower(A) each corner spans */
     int solve_corner_rows[4][2];/* rows of the one-column solve corner per jv_structure;
                                    [1]: factor and x both FP32, [0]: otherwise */
+    int spmv_wide_rows;         /* rows the spmv sums over a warp (spmv_long_row) */
 } jv_info;
 
 /* Fill *opt with the defaults above. */

@@ -44,7 +44,8 @@ class jv_options(ctypes.Structure):
                 ("milu", ctypes.c_int), ("sym_levels", ctypes.c_int),
                 ("stage_min_rows", ctypes.c_int), ("stage_max_density", ctypes.c_double),
                 ("stage_position", ctypes.c_double), ("er_corner", ctypes.c_int),
-                ("no_graphs", ctypes.c_int), ("exact", ctypes.c_int)]
+                ("no_graphs", ctypes.c_int), ("exact", ctypes.c_int),
+                ("spmv_long_row", ctypes.c_int)]
 
 
 class jv_info(ctypes.Structure):
@@ -55,7 +56,8 @@ class jv_info(ctypes.Structure):
                 ("npairs", ctypes.c_longlong), ("mode", ctypes.c_int), ("reorder", ctypes.c_int),
                 ("hybrid_launches", ctypes.c_int * 4), ("hybrid_launches_factor", ctypes.c_int),
                 ("corner_rows", ctypes.c_int * 2), ("corner_levels", ctypes.c_int * 2),
-                ("solve_corner_rows", (ctypes.c_int * 2) * 4)]
+                ("solve_corner_rows", (ctypes.c_int * 2) * 4),
+                ("spmv_wide_rows", ctypes.c_int)]
 
 
 class jv_krylov_opts(ctypes.Structure):
@@ -201,7 +203,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
                spin_timeout_cycles=0, fault_row=-1, sf_ctas_per_sm=0, sf_backoff_ns=0,
                band_rows=0, sf_gate_levels=None, milu=False, sym_levels=False,
                stage_min_rows=0, stage_max_density=0.0, stage_position=0.0, er_corner=False,
-               graphs=True, exact=False):
+               graphs=True, exact=False, spmv_long_row=0):
     """Analyse a CSR pattern (int32 CUDA tensors).  Returns a Handle.
     ``mode``: "level", "syncfree" or "hybrid" (the two-stage split of Sec. III-A,
     with the stage test ``stage_min_rows`` / ``stage_max_density`` /
@@ -233,6 +235,7 @@ def jv_analyze(rowptr, colidx, mode="syncfree", reorder=False, check=True, long_
     opt.er_corner = int(bool(er_corner))
     opt.no_graphs = int(not graphs)
     opt.exact = int(bool(exact))
+    opt.spmv_long_row = int(spmv_long_row)
     out = ctypes.c_void_p()
     stream = torch.cuda.current_stream(rowptr.device).cuda_stream
     with torch.cuda.device(rowptr.device):
@@ -380,7 +383,8 @@ def jv_get_info(h):
                 hybrid_launches=list(info.hybrid_launches),
                 hybrid_launches_factor=info.hybrid_launches_factor,
                 corner_rows=list(info.corner_rows), corner_levels=list(info.corner_levels),
-                solve_corner_rows=[list(r) for r in info.solve_corner_rows])
+                solve_corner_rows=[list(r) for r in info.solve_corner_rows],
+                spmv_wide_rows=info.spmv_wide_rows)
 
 
 def jv_get_levels(h, which="L"):

@@ -638,6 +638,12 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
         JV_TRY(halloc_n(h, &h->spmv_rows, n));
         JV_CUDA(cudaMemcpyAsync(h->spmv_rows, srows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
         JV_CUDA(cudaStreamSynchronize(s));
+        // the rows that split their sum over a warp come first in this order
+        const int wide = h->opt.spmv_long_row > 0 ? h->opt.spmv_long_row : kSpmvLongRow;
+        h->spmv_wide = 0;
+        if (!h->opt.exact)
+            while (h->spmv_wide < n && hrp[srows[h->spmv_wide] + 1] - hrp[srows[h->spmv_wide]] > wide)
+                ++h->spmv_wide;
     }
 
     // binned work lists: the four solves and the factor

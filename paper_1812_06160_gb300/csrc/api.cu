@@ -102,6 +102,7 @@ void jv_default_options(jv_options *opt) {
     opt->er_corner = 0;
     opt->no_graphs = 0;
     opt->exact = 0;
+    opt->spmv_long_row = 0;
 }
 
 void jv_default_krylov_opts(jv_krylov_opts *o) {
@@ -124,7 +125,10 @@ int jv_analyze(int n, int nnz, const int *rowptr, const int *colidx, const jv_op
         delete h;
         return JV_ERR_ARG;
     }
-    if (h->opt.long_row < 0 || h->opt.sf_ctas_per_sm < 0) { delete h; return JV_ERR_ARG; }
+    if (h->opt.long_row < 0 || h->opt.sf_ctas_per_sm < 0 || h->opt.spmv_long_row < 0) {
+        delete h;
+        return JV_ERR_ARG;
+    }
     if ((h->opt.milu || h->opt.sym_levels || h->opt.er_corner) && h->opt.band_rows > 0) {
         delete h;
         return JV_ERR_ARG;
@@ -306,6 +310,7 @@ int jv_get_info(jv_handle h, jv_info *info) {
         for (int k = 0; k < 4; ++k)
             info->solve_corner_rows[k][t] = h->scorner[k][t].use ? h->scorner[k][t].R : 0;
     }
+    info->spmv_wide_rows = h->spmv_wide;
     return JV_OK;
 }
 

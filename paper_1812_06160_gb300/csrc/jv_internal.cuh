@@ -20,6 +20,7 @@ constexpr long long kDefaultSpin = 1ll << 32;
 constexpr int kUnroll = 4;        // entries per lane per step (cooperative kernels)
 constexpr int kPoll = 8;          // largest poll window of the one-lane-per-row kernels
 constexpr int kLongDeps = 24;     // solve rows with more dependencies run one per warp
+constexpr int kSpmvLongRow = 128; // spmv rows longer than this sum over a warp (exact = 0)
 constexpr int kLaneSlot = 16;     // factor: 8-byte words of shared memory per one-lane row
 constexpr int kLaneSlotWide = 32; // the same, when many rows need 17..32 (e.g. MILU fill pairs)
 constexpr unsigned kHoldRounds = 64; // FP64 factor: poll rounds a ready row waits for its warp-mates
@@ -459,6 +460,7 @@ struct jv_handle_s {
     jv::SolveCorner scorner[4][2];           // per structure; [1]: lu and x both FP32
     int maxrow = 0;                          // longest row
     int *spmv_rows = nullptr;                // spmv: rows by length, longest first
+    int spmv_wide = 0;                       // spmv: the first spmv_wide of them sum over a warp
     // lazily allocated factor scratch (long rows / in-place copies)
     void *fscratch = nullptr;
     size_t fscratch_bytes = 0;

@@ -104,7 +104,16 @@ def _full_check(rp, ci, v, b, mode, dtype=np.float64, reorder=False, exact=False
                       f"largest relative error {close(got.cpu().numpy(), want)[1]:.2e}")
         x = W.rhs(len(rp) - 1, 1, seed=21)
         s = jv.jv_spmv(h, T(v), T(x)).cpu().numpy()
-        assert np.array_equal(s, O.spmv(rp, ci, v, x))
+        if jv.jv_get_info(h)["spmv_wide_rows"] == 0:
+            assert np.array_equal(s, O.spmv(rp, ci, v, x))
+        else:
+            # rows above spmv_long_row summed by lanes and a tree: within
+            # 1e-12 of the magnitude of their terms; the others bit-exact
+            ok, err = close_scaled(s, O.spmv(rp, ci, v, x), O.spmv(rp, ci, np.abs(v), np.abs(x)))
+            print(f"spmv: largest scaled error {err:.2e}")
+            assert ok, err
+            short = np.diff(rp) <= 128
+            assert np.array_equal(s[short], O.spmv(rp, ci, v, x)[short])
     else:
         assert max_rel(y.cpu().numpy(), oy) < 1e-4
         assert max_rel(z.cpu().numpy(), oz) < 1e-3

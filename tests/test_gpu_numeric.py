@@ -153,6 +153,42 @@ def test_spmv(case):
     assert np.all(np.abs(y32 - O.spmv(rp, ci, v, x)) <= 1e-5 * (scale + 1e-30))
 
 
+@pytest.mark.parametrize("long_row", [0, 8])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_spmv_default_mode(case, long_row):
+    # default mode: rows longer than spmv_long_row (128, or 8 here to reach
+    # the warp path on small matrices) sum by lanes and a fixed tree, within
+    # 1e-12 of the magnitude of their terms and identical run to run; the
+    # other rows keep the serial order bit for bit
+    _, rp, ci, v = case
+    n = len(rp) - 1
+    h = jv.jv_analyze(T(rp), T(ci), spmv_long_row=long_row)
+    thr = long_row or 128
+    lens = np.diff(rp)
+    assert jv.jv_get_info(h)["spmv_wide_rows"] == int((lens > thr).sum())
+    short = lens <= thr
+    x = W.rhs(n, 1, seed=3)
+    y0 = W.rhs(n, 1, seed=4)
+    for alpha, beta in ((1.0, 0.0), (-2.0, 0.5), (-1.0, 1.0)):
+        y = jv.jv_spmv(h, T(v), T(x), T(y0), alpha=alpha, beta=beta).cpu().numpy()
+        y2 = jv.jv_spmv(h, T(v), T(x), T(y0), alpha=alpha, beta=beta).cpu().numpy()
+        assert np.array_equal(y, y2)
+        want = O.spmv(rp, ci, v, x, y0, alpha=alpha, beta=beta)
+        assert np.array_equal(y[short], want[short])
+        scale = abs(alpha) * O.spmv(rp, ci, np.abs(v), np.abs(x)) + abs(beta) * np.abs(y0)
+        ok, err = close_scaled(y, want, scale)
+        assert ok, err
+        # values 8 bytes off a 16-byte boundary take the scalar-load kernel:
+        # the same bits
+        vu = T(np.concatenate([[0.0], v]))[1:]
+        yu = jv.jv_spmv(h, vu, T(x), T(y0), alpha=alpha, beta=beta).cpu().numpy()
+        assert np.array_equal(yu, y)
+    x32 = x.astype(np.float32)
+    y32 = jv.jv_spmv(h, T(v.astype(np.float32)), T(x32)).cpu().numpy()
+    want32 = O.spmv(rp, ci, v.astype(np.float32).astype(np.float64), x32.astype(np.float64))
+    assert np.all(np.abs(y32 - want32) <= 1e-5 * (O.spmv(rp, ci, np.abs(v), np.abs(x)) + 1e-30))
+
+
 OUTER_CASES = [c for c in CASES if c[0] in ("rand37", "rand250", "rand600", "rand1500", "lap5_33",
                                             "aniso5_41", "powerlaw6000", "band20_800")]
 

@@ -690,3 +690,36 @@ def test_solve_scale_bounds_other_summation_orders():
     assert np.all(scale >= np.abs(x) * (1 - 1e-12))
     ok, err = close_scaled(y, x, scale, rel=1e-13)
     assert ok, err
+
+
+def test_spmv_scale_bounds_lane_and_tree_order():
+    # the criterion the GPU tests apply to spmv rows summed by lanes and a
+    # tree: each of 32 lanes adds its share (entries l, l + 32, ...) in
+    # order, then a butterfly adds the partial sums.  That order stays within
+    # a few eps of the serial oracle relative to sum |a_rj x_j|, while a
+    # dropped term does not
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from jvutil import close_scaled
+    rp, ci, v = W.powerlaw(3000, kmin=4, kmax=1500, mean=40, seed_pattern=41, seed_values=42)
+    n = len(rp) - 1
+    x = W.rhs(n, 1, seed=43)
+    want = O.spmv(rp, ci, v, x)
+    scale = O.spmv(rp, ci, np.abs(v), np.abs(x))
+    got = np.empty(n)
+    dropped = want.copy()
+    for r in range(n):
+        part = [0.0] * 32
+        for q in range(rp[r], rp[r + 1]):
+            part[(q - rp[r]) % 32] += v[q] * x[ci[q]]
+        o = 16
+        while o:
+            part = [part[l] + part[l ^ o] for l in range(32)]
+            o >>= 1
+        got[r] = part[0]
+        if rp[r + 1] - rp[r] > 128:
+            dropped[r] = want[r] - v[rp[r]] * x[ci[rp[r]]]
+    assert (np.diff(rp) > 128).sum() > 50
+    ok, err = close_scaled(got, want, scale, rel=1e-13)
+    assert ok, err
+    assert not close_scaled(dropped, want, scale)[0]
