@@ -182,11 +182,21 @@ __global__ void k_pair_target(int np, const int2 *pairs, unsigned *key, unsigned
     idx[j] = (unsigned)j;
 }
 __global__ void k_tpairs(int np, const unsigned *sorted_idx, const unsigned *step, const int2 *pairs,
-                         int2 *tpairs) {
+                         const unsigned char *upd, int2 *tpairs) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
     const unsigned j = sorted_idx[s];
-    tpairs[s] = make_int2((int)step[j], pairs[j].y);
+    const int q = pairs[j].y;
+    tpairs[s] = make_int2((int)step[j], upd[q] ? ~q : q);   // ~q: an operand to await
+}
+
+// kpos[p] = the factor work-list position of row k, for every L entry
+// p = (r, k): where the pivot the entry divides by is published.
+__global__ void k_kpos(int n, const int *rowptr, const int *diag, const int *colidx,
+                       const int *ipos, int *kpos) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int p = rowptr[r], e = diag[r]; p < e; ++p) kpos[p] = ipos[colidx[p]];
 }
 
 // For every row: the depth of the dependency chain among its L entries (an
@@ -605,7 +615,7 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
         JV_TRY(radix_sort_pairs(pk, pv, pka, pva, np, bits_for(nnz - 1), prt, s));
         JV_TRY(keys_to_ptr(pk, np, h->tpair_ptr, nnz, s));
         count_launch();
-        k_tpairs<<<grid_for(np, kBlock), kBlock, 0, s>>>(np, pv, step, h->pairs, h->tpairs);
+        k_tpairs<<<grid_for(np, kBlock), kBlock, 0, s>>>(np, pv, step, h->pairs, h->upd, h->tpairs);
         JV_CHECK_LAUNCH();
         JV_CUDA(cudaStreamSynchronize(s));
     } else {
@@ -689,6 +699,11 @@ int build_all(jv_handle h, const int *rowptr_src, const int *colidx_src) {
     }
     JV_TRY(make_bins(h, h->ls[JV_LOWER], cost.data() + 4 * (size_t)n, h->fslot, fops.data(),
                      h->fbins, grp.data()));
+    JV_TRY(halloc_n(h, &h->kpos, nnz));
+    count_launch();
+    k_kpos<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->rowptr, h->diag, h->colidx, h->fbins.ipos,
+                                                  h->kpos);
+    JV_CHECK_LAUNCH();
     return plan_bands(h);
 }
 

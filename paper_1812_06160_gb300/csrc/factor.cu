@@ -85,17 +85,22 @@ struct FactorArgs {
     int fault_row;
     int milu;                     // several pairs of one step may target the diagonal
     const int *tpair_ptr;         // pairs by target (one-warp-per-row rows, pull form), or null
-    const int2 *tpairs;
+    const int2 *tpairs;           // (step p, operand q), q as ~q when it is awaited
+    const int *kpos;              // L entries: the work-list position of their pivot row
     void *pscratch;               // operands of rows too long for shared memory
     long long npairs_total;       // offset of the u_kk area in pscratch
     const unsigned char *row_pull; // per row: take the pull form
     const unsigned char *edepth;  // per L entry: depth of its in-row chain (255: 255 or more)
-    const int *colidx;            // column of every entry: the pivot row k of entry (r, k)
-    const int *ppos;              // work-list position of every row (where its pivot is published)
     const unsigned char *upd;     // 1: some step updates the entry (a pair operand to await)
     void *piv;                    // pivot of every row at its work-list position: u_kk, or
                                   // 1/u_kk with RCP (sentinel-filled in SYNCFREE mode)
+    int tree;                     // pull form: a U entry with more than kTreePairs updates
+                                  // sums them over the warp's lanes and a fixed tree
 };
+
+// a U entry of a pull-form row with more updates than this (a hub row's
+// diagonal: one update per L entry) sums them over the warp in tree mode
+constexpr int kTreePairs = 32;
 
 template <class T> struct RN;
 template <> struct RN<double> {
@@ -206,17 +211,16 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
 #pragma unroll
             for (int e = 0; e < S; ++e) {
                 if (e < len) v[e] = (TL)__ldg(vals + rs + e);
-                if (e < nl) kd[e] = __ldg(a.colidx + rs + e);
+                if (e < nl) kd[e] = __ldg(a.kpos + rs + e);       // the pivot's position
                 if (e < nl) se[e] = __ldg(a.pair_ptr + rs + e + 1);
                 if (e < np) pr[e] = __ldg(a.pairs + j0 + e);
             }
-            // the narrow slot: the pivots' positions, the update flags and the
-            // final-from-the-start operands as three batches of loads
+            // the narrow slot: the update flags, then the final-from-the-start
+            // operands, as two more batches of loads
             unsigned char up[S];
             TL sv[S];
 #pragma unroll
             for (int e = 0; e < S; ++e) {
-                if (e < nl) kd[e] = __ldg(a.ppos + kd[e]);         // pivot row -> its position
                 if (e < np) up[e] = __ldg(a.upd + pr[e].y);
             }
 #pragma unroll
@@ -248,7 +252,7 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
                 for (int i = 0; i < 16; ++i) {
                     const int e = h0 + i;
                     if (e < len) v[i] = (TL)__ldg(vals + rs + e);
-                    if (e < nl) kd[i] = __ldg(a.colidx + rs + e);
+                    if (e < nl) kd[i] = __ldg(a.kpos + rs + e);
                     if (e < nl) se[i] = __ldg(a.pair_ptr + rs + e + 1);
                     if (e < np) pr[i] = __ldg(a.pairs + j0 + e);
                 }
@@ -266,7 +270,6 @@ __device__ __forceinline__ void factor_lanes(const FactorArgs &a, int lo, int hi
             }
 #pragma unroll 8
             for (int e = 0; e < S; ++e) {
-                if (e < nl) OPOS(e) = __ldg(a.ppos + OPOS(e));    // pivot row -> its position
                 if (e < np && !__ldg(a.upd + OPOS(nl + e))) smask |= 1u << (nl + e);
             }
 #pragma unroll 8
@@ -463,7 +466,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         // rounds, the words that still held the sentinel
         auto where = [&](int e, bool &fixed) -> const TL * {
             fixed = false;
-            if (e < nl) return piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));   // pivot of step e
+            if (e < nl) return piv + __ldg(a.kpos + rs + e);   // pivot of step e
             const int q = __ldg(a.pairs + j0 + e - nl).y;                       // u_kq of a pair
             if (__ldg(a.upd + q)) return lu + q;
             fixed = true;                                  // final from the start: A's value
@@ -523,7 +526,7 @@ __device__ __forceinline__ void factor_warp(const FactorArgs &a, int pos, unsign
         if (fast) {
             ukk = uv[p];
         } else {
-            const TL *src = piv + __ldg(a.ppos + __ldg(a.colidx + rs + p));
+            const TL *src = piv + __ldg(a.kpos + rs + p);
             ukk = B::from(SF ? settle<TL>(src, first_read<TL, SF>(src), a, r, fail) : first_read<TL, SF>(src));
         }
         const TL lik = RCP ? w[p] * ukk : RN<TL>::div(w[p], ukk);
@@ -625,7 +628,7 @@ __device__ __forceinline__ void factor_group(const FactorArgs &a, int lo, int hi
     // words still missing (see factor_warp)
     auto where = [&](int e, bool &fixed) -> const TL * {
         fixed = false;
-        if (e < nl) return piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
+        if (e < nl) return piv + __ldg(a.kpos + rs + e);
         const int q = __ldg(a.pairs + j0 + e - nl).y;
         if (__ldg(a.upd + q)) return lu + q;
         fixed = true;
@@ -768,10 +771,10 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
             const int e = e0 + k * kWarp + lane;
             src[k] = nullptr;
             if (e < nl) {                                  // u_kk, or its reciprocal (RCP)
-                src[k] = piv + __ldg(a.ppos + __ldg(a.colidx + rs + e));
+                src[k] = piv + __ldg(a.kpos + rs + e);
             } else if (e < nl + nq) {                      // u_kq
                 const int q = __ldg(a.tpairs + s0 + e - nl).y;
-                if (__ldg(a.upd + q)) src[k] = static_cast<const TL *>(a.lu) + q;
+                if (q < 0) src[k] = static_cast<const TL *>(a.lu) + ~q;
                 else u[k] = B::to((TL)__ldg(vals + q));   // final from the start
             }
             if (src[k]) u[k] = first_read<TL, SF>(src[k]);
@@ -832,13 +835,47 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
         }
     }
     // U entries (the diagonal included): every one pulls its updates
+    if (!a.tree) {
 #pragma unroll 4
-    for (int e = nl + lane; e < len; e += kWarp) {
-        const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
-        TL acc = w[e];
-        for (int k = t0; k < t1; ++k)
-            acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
-        w[e] = acc;
+        for (int e = nl + lane; e < len; e += kWarp) {
+            const int t0 = __ldg(a.tpair_ptr + rs + e) - s0, t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
+            TL acc = w[e];
+            for (int k = t0; k < t1; ++k)
+                acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
+            w[e] = acc;
+        }
+    } else {
+        // tree mode: an entry with more than kTreePairs updates (a hub row's
+        // diagonal takes one per L entry: a chain of 1,000 dependent FP64
+        // operations on the power-law matrix) is summed by the whole warp --
+        // every lane its share in ascending step order, then a fixed
+        // butterfly, then added to a_q -- after the lane-strided pass over the
+        // others; deterministic, but not the serial order
+        for (int e0 = nl; e0 < len; e0 += kWarp) {
+            const int e = e0 + lane;
+            int t0 = 0, t1 = 0;
+            if (e < len) {
+                t0 = __ldg(a.tpair_ptr + rs + e) - s0;
+                t1 = __ldg(a.tpair_ptr + rs + e + 1) - s0;
+            }
+            const bool wide = t1 - t0 > kTreePairs;
+            if (e < len && !wide) {
+                TL acc = w[e];
+                for (int k = t0; k < t1; ++k)
+                    acc = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], acc);
+                w[e] = acc;
+            }
+            for (unsigned wm = __ballot_sync(0xffffffffu, wide); wm != 0u; wm &= wm - 1u) {
+                const int src = __ffs(wm) - 1;
+                const int k0 = __shfl_sync(0xffffffffu, t0, src), k1 = __shfl_sync(0xffffffffu, t1, src);
+                TL part = 0;
+                for (int k = k0 + lane; k < k1; k += kWarp)
+                    part = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], part);
+#pragma unroll
+                for (int off = kWarp / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+                if (lane == 0) w[e0 + src] += part;
+            }
+        }
     }
     __syncwarp();
     if (SF && __any_sync(0xffffffffu, fail)) return;
@@ -1025,14 +1062,14 @@ int run(jv_handle h, const void *vals, void *lu) {
     a.milu = h->opt.milu;
     a.tpair_ptr = h->tpair_ptr;
     a.tpairs = h->tpairs;
+    a.kpos = h->kpos;
     a.pscratch = h->pscratch;
     a.npairs_total = h->npairs;
     a.row_pull = h->row_pull;
     a.edepth = h->edepth;
-    a.colidx = h->colidx;
-    a.ppos = W.ipos;
     a.upd = h->upd;
     a.piv = h->piv;
+    a.tree = sizeof(TL) == 8 && !h->opt.exact;
     a.backoff_ns = sf_backoff(h);
     // the upper stage: levels [0, lend), above the Even-Rows corner if any
     const jv_dtype lu_t = sizeof(TL) == 8 ? JV_F64 : JV_F32;

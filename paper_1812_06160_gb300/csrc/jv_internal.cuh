@@ -448,7 +448,9 @@ struct jv_handle_s {
     int2 *pairs = nullptr;                   // [npairs] (t, q) absolute CSR positions
     int *kdiag = nullptr;                    // [nnz] diag[colidx[p]]: position of u_kk for p = (r, k)
     int *tpair_ptr = nullptr;                // [nnz + 1] the pairs grouped by target entry t:
-    int2 *tpairs = nullptr;                  // [npairs] (p, q) -- step p, operand q -- ascending p
+    int2 *tpairs = nullptr;                  // [npairs] (p, q) -- step p, operand q -- ascending p;
+                                             // q stored as ~q when some step updates u_kq
+                                             // (the operand is awaited, not read from A)
     unsigned char *row_pull = nullptr;       // [n] 1: a one-warp row takes the pull form
     unsigned char *edepth = nullptr;         // [nnz] L entries: depth of the in-row chain of steps
                                              // that update the entry (1: none; capped at 255)
@@ -456,6 +458,8 @@ struct jv_handle_s {
     long long ndyn_pairs = 0;                // pairs whose operand is updated (must be awaited)
     long long npairs = 0;
     jv::Bins fbins;                          // factor work list over the levels of lower(A)
+    int *kpos = nullptr;                     // [nnz] L entries p = (r, k): the factor work-list
+                                             // position of row k, where its pivot is published
     jv::CornerPlan corner[2];                // Even-Rows corner per factor dtype (jv_dtype)
     jv::SolveCorner scorner[4][2];           // per structure; [1]: lu and x both FP32
     int maxrow = 0;                          // longest row
