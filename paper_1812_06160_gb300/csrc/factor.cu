@@ -987,7 +987,10 @@ int run(jv_handle h, const void *vals, void *lu) {
     const LevelSet &L = h->ls[JV_LOWER];
     cudaStream_t s = h->stream;
     const bool inplace = vals == lu;
-    if (inplace || W.nlong > 0 || W.ngroup > 0) {
+    // the work area: rows of the warp and group forms, and rows of the band
+    // schedule over its kLaneSlot words (which the work list's one-lane slot,
+    // when it is the wide one, does not imply), that do not fit shared memory
+    if (inplace || W.nlong > 0 || W.ngroup > 0 || L.band.use) {
         int rc = ensure_scratch(h);
         if (rc) return rc;
     }

@@ -70,6 +70,24 @@ def test_syncfree_timeout_is_reported_and_context_survives(mode):
     torch.cuda.synchronize()
 
 
+def test_timeout_in_power_law_rows():
+    # a power-law row (the one-warp pull form) never publishes: the rows
+    # awaiting its pivot time out, report, and the context survives
+    rp, ci, v = W.powerlaw(3000, kmax=200, mean=12, seed_pattern=33, seed_values=34)
+    lens = np.diff(rp)
+    lower = [int((ci[rp[r]:rp[r + 1]] < r).sum()) for r in range(len(lens))]
+    # a mid-length row early in the order: many later rows depend on it
+    fault = next(r for r in range(len(lens)) if 20 <= lens[r] <= 40 and lower[r] >= 2)
+    h = analyze(jv, rp, ci, "syncfree", fault_row=fault, spin_timeout_cycles=2_000_000)
+    with pytest.raises(jv.JvError) as e:
+        jv.jv_ilu0_factor(h, T(v))
+    assert e.value.status == jv.JV_ERR_TIMEOUT and e.value.bad_row > fault
+    olu, _, _ = O.ilu0(rp, ci, v)
+    h2 = analyze(jv, rp, ci, "syncfree")
+    assert np.array_equal(jv.jv_ilu0_factor(h2, T(v)).cpu().numpy(), olu)
+    torch.cuda.synchronize()
+
+
 def test_async_status_accumulates_until_sync():
     rp = np.array([0, 2, 5, 7], dtype=np.int32)
     ci = np.array([0, 1, 0, 1, 2, 1, 2], dtype=np.int32)

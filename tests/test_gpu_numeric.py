@@ -51,6 +51,20 @@ def test_factor_fp64_reciprocal_pivots_within_1e12(case, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_factor_nine_point_rows(mode):
+    # a 9-point stencil: nearly every row needs 17..32 words (the wide
+    # one-lane slot, no one-warp rows), while the band schedule's one-thread
+    # rows over 16 words work in the global scratch area, which must exist
+    m = 30
+    offs = [(dx, dy, 0) for dx in (-1, 0, 1) for dy in (-1, 0, 1) if (dx, dy) != (0, 0)]
+    rp, ci, v = W.stencil((m, m, 1), offs, [-0.1] * 8, 1.0)
+    h = analyze(jv, rp, ci, mode)
+    olu, st, _ = O.ilu0(rp, ci, v)
+    assert st == 0
+    assert np.array_equal(jv.jv_ilu0_factor(h, T(v)).cpu().numpy(), olu)
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("nrhs", [1, 3, 33])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_solves_fp64_default_mode(case, nrhs, mode):
