@@ -757,6 +757,7 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
         uq = static_cast<TL *>(a.pscratch) + s0;
         ukk = static_cast<TL *>(a.pscratch) + a.npairs_total + rs;
     }
+#pragma unroll 4
     for (int e = lane; e < len; e += kWarp) w[e] = (TL)__ldg(vals + rs + e);
     if (SF && gate) sf_gate_wait(a.ticket, gate, a.timeout);
     TL *piv = static_cast<TL *>(a.piv);
@@ -801,9 +802,16 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
     // once, lane-strided with four entries in flight per lane; a row whose
     // chain is 255 deep or more takes chunks of 32 with waves inside a chunk
     int dmax = 0;
+#pragma unroll 8
     for (int e = lane; e < nl; e += kWarp) dmax = max(dmax, (int)__ldg(a.edepth + rs + e));
     dmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)dmax);
-    if (dmax < 255) {
+    if (dmax == 1) {
+        // no step of the row updates an L entry (the power-law rows): every
+        // l_rk from a_rk alone, without looking up the (empty) update lists
+#pragma unroll 4
+        for (int e = lane; e < nl; e += kWarp) w[e] = RCP ? w[e] * ukk[e] : RN<TL>::div(w[e], ukk[e]);
+        __syncwarp();
+    } else if (dmax < 255) {
         for (int d = 1; d <= dmax; ++d) {
 #pragma unroll 4
             for (int e = lane; e < nl; e += kWarp)
@@ -869,8 +877,23 @@ __device__ __forceinline__ void factor_warp_pull(const FactorArgs &a, int pos, u
                 const int src = __ffs(wm) - 1;
                 const int k0 = __shfl_sync(0xffffffffu, t0, src), k1 = __shfl_sync(0xffffffffu, t1, src);
                 TL part = 0;
-                for (int k = k0 + lane; k < k1; k += kWarp)
-                    part = RN<TL>::fms(w[__ldg(a.tpairs + s0 + k).x - rs], uq[k], part);
+                // the lane's share in ascending order, four entries' loads in flight
+                for (int k = k0 + lane; k < k1; k += 4 * kWarp) {
+                    int st[4];
+                    TL uv[4], lv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (k + i * kWarp < k1) {
+                            st[i] = __ldg(a.tpairs + s0 + k + i * kWarp).x - rs;
+                            uv[i] = uq[k + i * kWarp];
+                        }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (k + i * kWarp < k1) lv[i] = w[st[i]];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (k + i * kWarp < k1) part = RN<TL>::fms(lv[i], uv[i], part);
+                }
 #pragma unroll
                 for (int off = kWarp / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
                 if (lane == 0) w[e0 + src] += part;
