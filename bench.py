@@ -54,9 +54,9 @@ KERNEL_SOURCES = {"factor": ("factor.cu", "jv_internal.cuh"),
                   "lsolve": ("trisolve.cu", "jv_internal.cuh"),
                   "usolve": ("trisolve.cu", "jv_internal.cuh")}
 TRAFFIC = {
-    ("c2", "f64", "factor", "syncfree", False): (471_790_336, "1680f0e4d5d7"),
-    ("c2", "f64", "lsolve", "syncfree", False): (265_703_424, "e2a12b5e2481"),
-    ("c2", "f64", "usolve", "syncfree", False): (268_858_112, "e2a12b5e2481"),
+    ("c2", "f64", "factor", "syncfree", False): (463_433_216, "935fc88ac78b"),
+    ("c2", "f64", "lsolve", "syncfree", False): (265_663_232, "1cd43ef4689d"),
+    ("c2", "f64", "usolve", "syncfree", False): (268_394_496, "1cd43ef4689d"),
 }
 
 

@@ -155,18 +155,24 @@ typedef struct {
     int exact;                      /* 1: every FP64 result equals the serial algorithm's
                                        bit for bit: the factor divides by each pivot as
                                        Fig. 1 does, and every sum runs in the serial order.
-                                       0 (default), two departures, each within a few
-                                       units in the last place per operation:
+                                       0 (default), these departures, each deterministic
+                                       run to run and within a few units in the last
+                                       place per operation (sums: relative to the sum of
+                                       the terms' magnitudes):
                                        - the FP64 factor's row k computes 1/u_kk once, by
                                          Newton's iteration, when u_kk is final, and every
                                          multiplier is l_ik = a_ik * (1/u_kk) (the
                                          division sequence it replaces is the longest run
                                          of FP64 work on the critical path);
+                                       - an FP64 factor entry of a one-warp row that
+                                         receives more than 32 updates (a hub row's
+                                         diagonal) sums them over the warp's lanes, each
+                                         lane's share in ascending step order, then a
+                                         fixed tree, and adds the total to a_ij;
                                        - a solve row with more dependencies than long_row
-                                         splits its sum over the warp's lanes (each lane's
-                                         share in ascending order, then a fixed tree), so
-                                         its chain is about 1/32 as long; the result is
-                                         deterministic run to run.
+                                         splits its sum over the warp's lanes the same
+                                         way, so its chain is about 1/32 as long;
+                                       - spmv rows longer than spmv_long_row likewise.
                                        Either way the U / U^T solves form s / u_ii from
                                        1/u_ii, computed before a row's operands arrive,
                                        and one correction step (Markstein's), which gives
@@ -296,7 +302,12 @@ int jv_usolve_t(jv_handle h, jv_dtype lu_t, const void *lu, jv_dtype b_t,
 
 /* spmv (Sec. I; Sec. VI leaves it to future work): y = alpha A x + beta y.
  * vals[nnz], x[n], y[n] all of dtype t; beta == 0 never reads y.
- * x must not overlap y. */
+ * x must not overlap y.  Each row's products are added with one fused
+ * multiply-add each in ascending column order (the serial spmv's result),
+ * except, by default, rows longer than options.spmv_long_row, summed by the
+ * lanes of a warp and a fixed tree (jv_options.exact).  16-byte aligned
+ * vals take wider loads on matrices with rows over 32 entries (same
+ * result). */
 int jv_spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y,
             double alpha, double beta);
 
