@@ -466,7 +466,11 @@ def main(argv=None):
     dom = max(avg, key=avg.get)
     peak, peak_kind = measured_peaks()
     achieved = model[dom] / (avg[dom] * 1e-3) / 1e9
-    tr = TRAFFIC.get((a.config, a.dtype, dom, a.mode, a.reorder))
+    # the captured variant only: the default factor at full size (no MILU,
+    # fill, corner, band, symmetric levels, stage option or exact division)
+    plain = not (a.milu or a.fill_level or a.er_corner or a.sym_levels or a.exact or
+                 a.band_rows or a.scale or a.stage_min_rows)
+    tr = TRAFFIC.get((a.config, a.dtype, dom, a.mode, a.reorder)) if plain else None
     traffic = tr[0] if tr and dom in KERNEL_SOURCES and tr[1] == _src_hash(KERNEL_SOURCES[dom]) \
         else None
     kern = {}
