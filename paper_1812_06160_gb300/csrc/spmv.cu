@@ -76,10 +76,10 @@ __device__ __forceinline__ void spmv_row_warp(int r, const int *__restrict__ row
 // start first.  A lane streams its row in chunks of U entries through a
 // three-stage pipeline -- indices and values of chunk c+2 loading, x of chunk
 // c+1 being gathered, chunk c being summed -- so a long row's loads stay
-// ahead of its chain.  FP64 matrices whose rows are all short (at most 32
-// entries) take chunks of 2 and six CTAs per SM (fewer registers, more warps
-// to hide the gathers: 7-point 128^3 spmv 68 -> 52 us); longer rows take
-// chunks of 4 and four CTAs per SM (the power-law matrix: 0.80 -> 0.62 ms).
+// ahead of its chain.  Short rows take short chunks and more CTAs per SM
+// (fewer registers, more warps to hide the gathers; see spmv() for the
+// choice by the longest row); long rows take chunks of 4 and four CTAs per
+// SM (the power-law matrix: 0.80 -> 0.62 ms).
 // WIDE: the first nwide rows of the order (the longest, default mode) take a
 // warp each (spmv_row_warp) and the remaining rows follow one per lane.
 template <class T, int U, int MINB, bool WIDE>
@@ -325,8 +325,13 @@ int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, doub
                                                        (T_)beta, ha, hb);
 #define ARGS_k_spmv
 #define ARGS_k_spmv_quad h->nnz,
+    // chunk and CTAs per SM by the longest row: stencils of at most 8 entries
+    // take single-entry chunks and eight CTAs per SM (7-point 128^3 FP64 52 ->
+    // 50 us) and, in FP32, chunks of 4 and six CTAs (46 -> 38 us); the
+    // 27-point rows keep longer chunks (the single-entry form: 85 -> 140 us)
     if (t == JV_F64) {
-        if (nw == 0 && h->maxrow <= 32) { JV_SPMV(k_spmv, double, 2, 6, false) }
+        if (nw == 0 && h->maxrow <= 8) { JV_SPMV(k_spmv, double, 1, 8, false) }
+        else if (nw == 0 && h->maxrow <= 32) { JV_SPMV(k_spmv, double, 2, 6, false) }
         else if (quad && nw > 0) { JV_SPMV(k_spmv_quad, double, 4, 4, true) }
         else if (quad) { JV_SPMV(k_spmv_quad, double, 4, 4, false) }
         else if (nw > 0) { JV_SPMV(k_spmv, double, 4, 4, true) }
@@ -335,6 +340,7 @@ int spmv(jv_handle h, jv_dtype t, const void *vals, const void *x, void *y, doub
         if (quad && nw > 0) { JV_SPMV(k_spmv_quad, float, 8, 4, true) }
         else if (quad) { JV_SPMV(k_spmv_quad, float, 8, 4, false) }
         else if (nw > 0) { JV_SPMV(k_spmv, float, 8, 4, true) }
+        else if (h->maxrow <= 8) { JV_SPMV(k_spmv, float, 4, 6, false) }
         else { JV_SPMV(k_spmv, float, 8, 4, false) }
     } else
         return JV_ERR_ARG;
