@@ -723,3 +723,52 @@ def test_spmv_scale_bounds_lane_and_tree_order():
     ok, err = close_scaled(got, want, scale, rel=1e-13)
     assert ok, err
     assert not close_scaled(dropped, want, scale)[0]
+
+
+def _fma(a, b, c):
+    # one correctly rounded a*b + c: exact rational arithmetic, then a single
+    # rounding (Fraction -> float rounds to nearest)
+    from fractions import Fraction
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def test_factor_diagonal_tree_order_within_bound():
+    # the default FP64 factor sums a hub row's diagonal updates (more than 32)
+    # over 32 lanes and a butterfly.  On a power-law matrix: the oracle's
+    # diagonal is the serial chain of fused multiply-adds over its final l_ik
+    # and u_ki (bit for bit), the lane-and-tree order stays within the 1e-12
+    # bound the GPU tests apply, and a dropped update does not
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from jvutil import close
+    rp, ci, v = W.powerlaw(800, kmin=4, kmax=300, mean=24, seed_pattern=51, seed_values=52)
+    n = len(rp) - 1
+    diag = O.diag_ptr(rp, ci)
+    lu, st, _ = O.ilu0(rp, ci, v, diag)
+    assert st == O.OK
+    pos = [dict(zip(ci[rp[r]:rp[r + 1]].tolist(), range(rp[r], rp[r + 1]))) for r in range(n)]
+    serial, tree, dropped = lu.copy(), lu.copy(), lu.copy()
+    hubs = 0
+    for r in range(n):
+        terms = [(lu[p], lu[pos[k][r]]) for p, k in zip(range(rp[r], diag[r]), ci[rp[r]:diag[r]])
+                 if r in pos[k]]
+        d = v[diag[r]]
+        for l, u in terms:
+            d = _fma(-l, u, d)
+        serial[diag[r]] = d
+        if len(terms) > 32:
+            hubs += 1
+            part = [0.0] * 32
+            for t, (l, u) in enumerate(terms):
+                part[t % 32] = _fma(-l, u, part[t % 32])
+            o = 16
+            while o:
+                part = [part[i] + part[i ^ o] for i in range(32)]
+                o >>= 1
+            tree[diag[r]] = v[diag[r]] + part[0]
+            dropped[diag[r]] = tree[diag[r]] + terms[0][0] * terms[0][1]
+    assert hubs > 20
+    assert np.array_equal(serial, lu)
+    ok, err = close(tree, lu)
+    assert ok, err
+    assert not close(dropped, lu)[0]
